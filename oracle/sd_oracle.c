@@ -1,0 +1,871 @@
+/*
+ * Smooth-distance oracle: a plain, slow FP64 CPU reference.
+ *
+ * TEST INFRASTRUCTURE. Only tests/, __graft_entry__.smoke() and bench.py's
+ * CPU-baseline leg load this library; the CUDA library shares no code with
+ * it and never links it.
+ *
+ * What it computes (Madan & Levin, "Fast Evaluation of Smooth Distance
+ * Constraints on Co-Dimensional Geometry"):
+ *   - exact point/segment/triangle distances and closest-point barycentrics
+ *     (App. B, Eq. distsq / dgrad);
+ *   - the blending weights w_i = (A w~_i)^S with the App. C polynomials (the
+ *     coefficient bases are solved in numpy and passed in) and the gradient
+ *     chain rule of Eq. dw_new, attenuation S = alpha / max(alpha, alpha_U)
+ *     (Sec. 3.3);
+ *   - the LogSumExp smooth distance and its gradient (Eq. 3 / Eq. 4) by brute
+ *     force over all primitives, evaluated in shifted form
+ *     t_i = ln w_i - alpha d_i, m = max t_i;
+ *   - the conservative Barnes-Hut evaluation of Alg. 1 / Alg. 2 with the far
+ *     field of App. D (expansion centre = closest point of the node's AABB),
+ *     on a binary radix tree over Morton codes that this file builds itself
+ *     (top-down split at the highest differing key bit).
+ *
+ * Readings of the paper that this file takes (each listed in the design
+ * notes): epsilon of Alg. 2 is 0 (the shifted sum is >= 1); incidence counts
+ * are per slot; isolated triangles (v_i = 1) use w~ = 1; w~ is clamped to at
+ * least 1e-6; far-field weight of a node is 1 if it holds only points, else
+ * max(A_E, A_T)^S; the Barnes-Hut test is applied before the leaf test.
+ *
+ * Compile: gcc -O2 -ffp-contract=off -fPIC -shared -pthread sd_oracle.c -lm
+ * (no FMA contraction: the FP32 Morton codes and FP32 Barnes-Hut decisions
+ * below must be the exact IEEE results of the written operation order).
+ */
+#include <math.h>
+#include <pthread.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+enum { K_POINT = 0, K_SEG = 1, K_TRI = 2 };
+
+typedef struct {
+    int kind;
+    int64_t v[3];      /* indices into the scene's combined vertex array */
+    double pa, pb;     /* segment: u, v = 1/|N_i0|, 1/|N_i1|; triangle: 1/v_i, 1/e_i */
+    int isolated;      /* triangle whose largest vertex valence is 1 */
+} prim_t;
+
+typedef struct {
+    int64_t nv;
+    double *V;         /* combined vertices (points, edge-mesh V, triangle-mesh V), FP64 */
+    float *Vf;         /* the same vertices as given (fp32) */
+    int64_t n, np, ne, nt;
+    prim_t *P;
+    double A_E, A_T;
+    double ebasis[5][3];
+    double tbasis[36][3];
+    int texp[36][2];
+    /* tree */
+    int L;
+    int64_t nb;
+    uint64_t *codes;   /* Morton code per primitive, original order */
+    int64_t *sorted;   /* primitive index in sorted order */
+    int32_t *left, *right;      /* internal nodes (nb-1); leaf child = -(bucket+1) */
+    float (*nlo)[3], (*nhi)[3]; /* internal node AABBs */
+    int64_t *ncount;
+    int *npts_only;
+    float (*llo)[3], (*lhi)[3]; /* leaf (bucket) AABBs */
+    int64_t *lcount;
+    int *lpts_only;
+    float slo[3], shi[3];       /* scene AABB */
+} scene_t;
+
+/* ------------------------------------------------------------------------ */
+/* small vector helpers                                                     */
+/* ------------------------------------------------------------------------ */
+static double dot3(const double *a, const double *b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+static void sub3(double *o, const double *a, const double *b) { o[0] = a[0] - b[0]; o[1] = a[1] - b[1]; o[2] = a[2] - b[2]; }
+
+/* ------------------------------------------------------------------------ */
+/* scene construction: primitives, incidence counts (valences)              */
+/* ------------------------------------------------------------------------ */
+static int cmp_u64pair(const void *a, const void *b)
+{
+    const uint64_t *x = (const uint64_t *)a, *y = (const uint64_t *)b;
+    return (x[0] < y[0]) ? -1 : (x[0] > y[0]) ? 1 : 0;
+}
+
+void *orc_scene_new(const float *pts, int64_t np,
+                    const float *ev, int64_t nev, const int32_t *E, int64_t ne,
+                    const float *tv, int64_t ntv, const int32_t *F, int64_t nf,
+                    const double *ebasis15, const double *tbasis108)
+{
+    scene_t *s = (scene_t *)calloc(1, sizeof(scene_t));
+    s->np = np; s->ne = ne; s->nt = nf;
+    s->n = np + ne + nf;
+    s->nv = np + nev + ntv;
+    s->V = (double *)malloc(sizeof(double) * 3 * (s->nv ? s->nv : 1));
+    s->Vf = (float *)malloc(sizeof(float) * 3 * (s->nv ? s->nv : 1));
+    for (int64_t i = 0; i < np * 3; ++i) { s->Vf[i] = pts[i]; }
+    for (int64_t i = 0; i < nev * 3; ++i) { s->Vf[np * 3 + i] = ev[i]; }
+    for (int64_t i = 0; i < ntv * 3; ++i) { s->Vf[(np + nev) * 3 + i] = tv[i]; }
+    for (int64_t i = 0; i < s->nv * 3; ++i) s->V[i] = (double)s->Vf[i];
+    memcpy(s->ebasis, ebasis15, sizeof(s->ebasis));
+    memcpy(s->tbasis, tbasis108, sizeof(s->tbasis));
+    {
+        int j = 0;
+        for (int a = 0; a < 8; ++a)
+            for (int b = 0; b < 8; ++b)
+                if (a + b <= 7) { s->texp[j][0] = a; s->texp[j][1] = b; ++j; }
+    }
+    s->P = (prim_t *)calloc((size_t)(s->n ? s->n : 1), sizeof(prim_t));
+    int64_t k = 0;
+    for (int64_t i = 0; i < np; ++i, ++k) {
+        s->P[k].kind = K_POINT; s->P[k].v[0] = i;
+    }
+    /* edge mesh: |N_k| = number of edge slots that reference vertex k */
+    s->A_E = 1.0;
+    if (ne > 0) {
+        int64_t *cnt = (int64_t *)calloc((size_t)nev, sizeof(int64_t));
+        for (int64_t i = 0; i < ne; ++i) { cnt[E[2 * i]]++; cnt[E[2 * i + 1]]++; }
+        int64_t amax = 0;
+        for (int64_t i = 0; i < nev; ++i) if (cnt[i] > amax) amax = cnt[i];
+        s->A_E = (double)amax;
+        for (int64_t i = 0; i < ne; ++i, ++k) {
+            s->P[k].kind = K_SEG;
+            s->P[k].v[0] = np + E[2 * i];
+            s->P[k].v[1] = np + E[2 * i + 1];
+            s->P[k].pa = 1.0 / (double)cnt[E[2 * i]];
+            s->P[k].pb = 1.0 / (double)cnt[E[2 * i + 1]];
+        }
+        free(cnt);
+    }
+    /* triangle mesh: vertex valence = triangle slots referencing the vertex;
+       edge valence = triangle edge slots with the same unordered vertex pair */
+    s->A_T = 1.0;
+    if (nf > 0) {
+        int64_t *vc = (int64_t *)calloc((size_t)ntv, sizeof(int64_t));
+        for (int64_t i = 0; i < nf * 3; ++i) vc[F[i]]++;
+        uint64_t *ek = (uint64_t *)malloc(sizeof(uint64_t) * 2 * 3 * nf);
+        for (int64_t i = 0; i < nf; ++i)
+            for (int j = 0; j < 3; ++j) {
+                uint64_t a = (uint64_t)F[3 * i + j], b = (uint64_t)F[3 * i + (j + 1) % 3];
+                uint64_t lo = a < b ? a : b, hi = a < b ? b : a;
+                ek[2 * (3 * i + j)] = (lo << 32) | hi;
+                ek[2 * (3 * i + j) + 1] = (uint64_t)(3 * i + j);
+            }
+        qsort(ek, (size_t)(3 * nf), 2 * sizeof(uint64_t), cmp_u64pair);
+        int64_t *ecnt = (int64_t *)malloc(sizeof(int64_t) * 3 * nf);
+        for (int64_t i = 0; i < 3 * nf;) {
+            int64_t j = i;
+            while (j < 3 * nf && ek[2 * j] == ek[2 * i]) ++j;
+            for (int64_t t = i; t < j; ++t) ecnt[ek[2 * t + 1]] = j - i;
+            i = j;
+        }
+        int64_t amax = 0;
+        for (int64_t i = 0; i < nf; ++i, ++k) {
+            int64_t vmax = 0, emax = 0;
+            for (int j = 0; j < 3; ++j) {
+                if (vc[F[3 * i + j]] > vmax) vmax = vc[F[3 * i + j]];
+                if (ecnt[3 * i + j] > emax) emax = ecnt[3 * i + j];
+            }
+            if (vmax > amax) amax = vmax;
+            s->P[k].kind = K_TRI;
+            for (int j = 0; j < 3; ++j) s->P[k].v[j] = np + nev + F[3 * i + j];
+            s->P[k].pa = 1.0 / (double)vmax;
+            s->P[k].pb = 1.0 / (double)emax;
+            s->P[k].isolated = (vmax == 1);
+        }
+        s->A_T = (double)amax;
+        free(vc); free(ek); free(ecnt);
+    }
+    return s;
+}
+
+static void tree_free(scene_t *s)
+{
+    free(s->codes); free(s->sorted); free(s->left); free(s->right);
+    free(s->nlo); free(s->nhi); free(s->ncount); free(s->npts_only);
+    free(s->llo); free(s->lhi); free(s->lcount); free(s->lpts_only);
+    s->codes = NULL; s->sorted = NULL; s->left = s->right = NULL;
+    s->nlo = s->nhi = NULL; s->ncount = NULL; s->npts_only = NULL;
+    s->llo = s->lhi = NULL; s->lcount = NULL; s->lpts_only = NULL;
+    s->nb = 0;
+}
+
+void orc_scene_free(void *h)
+{
+    scene_t *s = (scene_t *)h;
+    if (!s) return;
+    tree_free(s);
+    free(s->V); free(s->Vf); free(s->P); free(s);
+}
+
+void orc_scene_info(void *h, double *out)
+{
+    scene_t *s = (scene_t *)h;
+    out[0] = s->A_E; out[1] = s->A_T;
+    out[2] = (double)s->n; out[3] = (double)s->np; out[4] = (double)s->ne; out[5] = (double)s->nt;
+}
+
+void orc_prim_params(void *h, double *out, int32_t *kind, int32_t *iso)
+{
+    scene_t *s = (scene_t *)h;
+    for (int64_t i = 0; i < s->n; ++i) {
+        out[2 * i] = s->P[i].pa; out[2 * i + 1] = s->P[i].pb;
+        kind[i] = s->P[i].kind; iso[i] = s->P[i].isolated;
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* exact distances (App. B)                                                 */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    double d;          /* distance */
+    double gd[3];      /* gradient of d w.r.t. q (Eq. dgrad), 0 when d == 0 */
+    double phi[2];     /* barycentric coordinates of the closest point */
+    double gphi[2][3]; /* gradients of phi w.r.t. q */
+    int degenerate;    /* zero-area triangle: weight gradient forced to 0 */
+} near_t;
+
+/* closest point of segment a + t e, t in [0, 1]; returns t and whether the
+   unconstrained parameter was clamped (then dt/dq = 0) */
+static double seg_param(const double *a, const double *e, const double *q, int *clamped)
+{
+    double ee = dot3(e, e);
+    if (ee == 0.0) { *clamped = 1; return 0.0; }
+    double ap[3]; sub3(ap, q, a);
+    double t = dot3(ap, e) / ee;
+    if (t <= 0.0) { *clamped = 1; return 0.0; }
+    if (t >= 1.0) { *clamped = 1; return 1.0; }
+    *clamped = 0;
+    return t;
+}
+
+static void finish_dist(near_t *r, const double *q, const double *pi)
+{
+    double dv[3]; sub3(dv, q, pi);
+    r->d = sqrt(dot3(dv, dv));
+    for (int j = 0; j < 3; ++j) r->gd[j] = r->d > 0.0 ? dv[j] / r->d : 0.0;
+}
+
+static void near_point(const double *p, const double *q, near_t *r)
+{
+    memset(r, 0, sizeof(*r));
+    finish_dist(r, q, p);
+}
+
+static void near_segment(const double *a, const double *b, const double *q, near_t *r)
+{
+    memset(r, 0, sizeof(*r));
+    double e[3]; sub3(e, b, a);
+    int cl;
+    double t = seg_param(a, e, q, &cl);
+    double pi[3] = {a[0] + t * e[0], a[1] + t * e[1], a[2] + t * e[2]};
+    r->phi[0] = t;
+    if (!cl) {
+        double ee = dot3(e, e);
+        for (int j = 0; j < 3; ++j) r->gphi[0][j] = e[j] / ee;
+    }
+    finish_dist(r, q, pi);
+}
+
+/* Point-triangle distance as the QP of Eq. distsq over the simplex
+   f(phi) = (1 - phi1 - phi2) v0 + phi1 v1 + phi2 v2: the unconstrained
+   minimiser (2x2 normal equations) if it lies in the triangle, otherwise the
+   best of the three boundary segments (the minimiser of a convex QP that is
+   not interior lies on the boundary). */
+static void near_triangle(const double *v0, const double *v1, const double *v2, const double *q, near_t *r)
+{
+    memset(r, 0, sizeof(*r));
+    double e1[3], e2[3], ap[3];
+    sub3(e1, v1, v0); sub3(e2, v2, v0); sub3(ap, q, v0);
+    double g00 = dot3(e1, e1), g01 = dot3(e1, e2), g11 = dot3(e2, e2);
+    double det = g00 * g11 - g01 * g01;
+    double scale = g00 * g11;
+    int degenerate = !(det > 1e-14 * scale) || scale == 0.0;
+    if (!degenerate) {
+        double r0 = dot3(ap, e1), r1 = dot3(ap, e2);
+        double p1 = (g11 * r0 - g01 * r1) / det;
+        double p2 = (g00 * r1 - g01 * r0) / det;
+        if (p1 >= 0.0 && p2 >= 0.0 && p1 + p2 <= 1.0) {
+            double pi[3];
+            for (int j = 0; j < 3; ++j) pi[j] = v0[j] + p1 * e1[j] + p2 * e2[j];
+            r->phi[0] = p1; r->phi[1] = p2;
+            for (int j = 0; j < 3; ++j) {
+                r->gphi[0][j] = (g11 * e1[j] - g01 * e2[j]) / det;
+                r->gphi[1][j] = (g00 * e2[j] - g01 * e1[j]) / det;
+            }
+            finish_dist(r, q, pi);
+            return;
+        }
+    }
+    /* boundary: edges v0v1 (phi = (t, 0)), v1v2 (phi = (1 - t, t)), v0v2 (phi = (0, t)) */
+    near_t best; best.d = INFINITY;
+    for (int k = 0; k < 3; ++k) {
+        const double *a = k == 0 ? v0 : (k == 1 ? v1 : v0);
+        const double *b = k == 0 ? v1 : (k == 1 ? v2 : v2);
+        near_t c;
+        memset(&c, 0, sizeof(c));
+        double e[3]; sub3(e, b, a);
+        int cl;
+        double t = seg_param(a, e, q, &cl);
+        double pi[3] = {a[0] + t * e[0], a[1] + t * e[1], a[2] + t * e[2]};
+        finish_dist(&c, q, pi);
+        double ee = dot3(e, e);
+        double gt[3] = {0, 0, 0};
+        if (!cl) for (int j = 0; j < 3; ++j) gt[j] = e[j] / ee;
+        if (k == 0) { c.phi[0] = t; c.phi[1] = 0.0; for (int j = 0; j < 3; ++j) c.gphi[0][j] = gt[j]; }
+        if (k == 1) { c.phi[0] = 1.0 - t; c.phi[1] = t; for (int j = 0; j < 3; ++j) { c.gphi[0][j] = -gt[j]; c.gphi[1][j] = gt[j]; } }
+        if (k == 2) { c.phi[0] = 0.0; c.phi[1] = t; for (int j = 0; j < 3; ++j) c.gphi[1][j] = gt[j]; }
+        if (c.d < best.d) best = c;
+    }
+    *r = best;
+    r->degenerate = degenerate;
+}
+
+/* ------------------------------------------------------------------------ */
+/* weights (Sec. 3.3, App. C)                                               */
+/* ------------------------------------------------------------------------ */
+#define W_MIN 1e-6
+
+/* w~ and dw~/dphi for a primitive at barycentrics phi */
+static void weight_tilde(const scene_t *s, const prim_t *p, const double *phi, double *wt, double *dw)
+{
+    dw[0] = dw[1] = 0.0;
+    if (p->kind == K_SEG) {
+        double c[5];
+        for (int k = 0; k < 5; ++k) c[k] = s->ebasis[k][0] * p->pa + s->ebasis[k][1] * p->pb + s->ebasis[k][2];
+        double x = phi[0], w = 0.0, d = 0.0;
+        for (int k = 0; k < 5; ++k) w += c[k] * pow(x, k);
+        for (int k = 1; k < 5; ++k) d += k * c[k] * pow(x, k - 1);
+        *wt = w; dw[0] = d;
+    } else if (p->kind == K_TRI) {
+        if (p->isolated) { *wt = 1.0; return; }
+        double x = phi[0], y = phi[1], w = 0.0, d1 = 0.0, d2 = 0.0;
+        double rhs[3] = {p->pa, p->pb, 1.0 - p->pa};
+        for (int j = 0; j < 36; ++j) {
+            double c = s->tbasis[j][0] * rhs[0] + s->tbasis[j][1] * rhs[1] + s->tbasis[j][2] * rhs[2];
+            int a = s->texp[j][0], b = s->texp[j][1];
+            w += c * pow(x, a) * pow(y, b);
+            if (a > 0) d1 += c * a * pow(x, a - 1) * pow(y, b);
+            if (b > 0) d2 += c * b * pow(x, a) * pow(y, b - 1);
+        }
+        *wt = w; dw[0] = d1; dw[1] = d2;
+    } else {
+        *wt = 1.0;
+    }
+    if (*wt < W_MIN) { *wt = W_MIN; dw[0] = dw[1] = 0.0; }
+}
+
+/* One exact contribution: t = ln w - alpha d and the vector
+   grad d - (1/alpha) grad(w) / w  (so that the numerator of Eq. 4 is
+   sum_i w_i e^{-alpha d_i} * vector_i). */
+typedef struct { double t; double v[3]; } term_t;
+
+typedef struct {
+    double alpha, S;
+    int paper_metric;
+} params_t;
+
+static void prim_near(const scene_t *s, const prim_t *p, const double *q, near_t *nr)
+{
+    const double *V = s->V;
+    if (p->kind == K_POINT) near_point(V + 3 * p->v[0], q, nr);
+    else if (p->kind == K_SEG) near_segment(V + 3 * p->v[0], V + 3 * p->v[1], q, nr);
+    else near_triangle(V + 3 * p->v[0], V + 3 * p->v[1], V + 3 * p->v[2], q, nr);
+}
+
+static term_t prim_term(const scene_t *s, const prim_t *p, const double *q, const params_t *pr,
+                        near_t *nr_out, double *wt_out, double *gwt_out)
+{
+    near_t nr;
+    prim_near(s, p, q, &nr);
+    term_t T;
+    double wt = 1.0, dw[2] = {0, 0}, gwt[3] = {0, 0, 0};
+    if (p->kind != K_POINT) {
+        weight_tilde(s, p, nr.phi, &wt, dw);
+        if (!nr.degenerate)
+            for (int j = 0; j < 3; ++j) gwt[j] = dw[0] * nr.gphi[0][j] + dw[1] * nr.gphi[1][j];
+        if (pr->paper_metric)
+            for (int j = 0; j < 3; ++j) gwt[j] /= pr->alpha;
+    }
+    if (p->kind == K_POINT) {
+        T.t = -pr->alpha * nr.d;
+        for (int j = 0; j < 3; ++j) T.v[j] = nr.gd[j];
+    } else {
+        double A = p->kind == K_SEG ? s->A_E : s->A_T;
+        double lw = pr->S * log(A * wt);
+        T.t = lw - pr->alpha * nr.d;
+        for (int j = 0; j < 3; ++j) T.v[j] = nr.gd[j] - (pr->S * gwt[j] / wt) / pr->alpha;
+    }
+    if (nr_out) *nr_out = nr;
+    if (wt_out) *wt_out = wt;
+    if (gwt_out) for (int j = 0; j < 3; ++j) gwt_out[j] = gwt[j];
+    return T;
+}
+
+/* out: d, gd[3], phi[2], wt, gwt[3], t, v[3]  (14 doubles) */
+void orc_prim_eval(void *h, int64_t i, double alpha, double alpha_u, int paper_metric,
+                   const double *q, double *out)
+{
+    scene_t *s = (scene_t *)h;
+    params_t pr = {alpha, alpha / (alpha > alpha_u ? alpha : alpha_u), paper_metric};
+    near_t nr; double wt, gwt[3];
+    term_t T = prim_term(s, &s->P[i], q, &pr, &nr, &wt, gwt);
+    out[0] = nr.d;
+    for (int j = 0; j < 3; ++j) out[1 + j] = nr.gd[j];
+    out[4] = nr.phi[0]; out[5] = nr.phi[1];
+    out[6] = wt;
+    for (int j = 0; j < 3; ++j) out[7 + j] = gwt[j];
+    out[10] = T.t;
+    for (int j = 0; j < 3; ++j) out[11 + j] = T.v[j];
+}
+
+/* LogSumExp of Eq. 3 / Eq. 4 over a list of terms (shifted by the max) */
+static void lse_finish(const term_t *T, int64_t n, double alpha, double *val, double *grad)
+{
+    if (n == 0) { *val = INFINITY; grad[0] = grad[1] = grad[2] = 0.0; return; }
+    double m = -INFINITY;
+    for (int64_t i = 0; i < n; ++i) if (T[i].t > m) m = T[i].t;
+    double sum = 0.0, g[3] = {0, 0, 0};
+    for (int64_t i = 0; i < n; ++i) {
+        double e = exp(T[i].t - m);
+        sum += e;
+        for (int j = 0; j < 3; ++j) g[j] += e * T[i].v[j];
+    }
+    *val = -(m + log(sum)) / alpha;
+    for (int j = 0; j < 3; ++j) grad[j] = g[j] / sum;
+}
+
+/* ------------------------------------------------------------------------ */
+/* thread pool over queries                                                 */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    void (*fn)(void *ctx, int64_t i, void *scratch);
+    void *ctx;
+    int64_t m, next;
+    size_t scratch_bytes;
+    pthread_mutex_t mu;
+} pool_t;
+
+static void *pool_worker(void *arg)
+{
+    pool_t *p = (pool_t *)arg;
+    void *scratch = p->scratch_bytes ? malloc(p->scratch_bytes) : NULL;
+    for (;;) {
+        pthread_mutex_lock(&p->mu);
+        int64_t i0 = p->next;
+        p->next += 16;
+        pthread_mutex_unlock(&p->mu);
+        if (i0 >= p->m) break;
+        int64_t i1 = i0 + 16 < p->m ? i0 + 16 : p->m;
+        for (int64_t i = i0; i < i1; ++i) p->fn(p->ctx, i, scratch);
+    }
+    free(scratch);
+    return NULL;
+}
+
+static void run_pool(void (*fn)(void *, int64_t, void *), void *ctx, int64_t m, size_t scratch, int nthreads)
+{
+    pool_t p;
+    p.fn = fn; p.ctx = ctx; p.m = m; p.next = 0; p.scratch_bytes = scratch;
+    pthread_mutex_init(&p.mu, NULL);
+    if (nthreads < 1) nthreads = 1;
+    pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * nthreads);
+    for (int t = 0; t < nthreads; ++t) pthread_create(&th[t], NULL, pool_worker, &p);
+    for (int t = 0; t < nthreads; ++t) pthread_join(th[t], NULL);
+    free(th);
+    pthread_mutex_destroy(&p.mu);
+}
+
+/* ------------------------------------------------------------------------ */
+/* brute force (Eq. 3 / Eq. 4 over every primitive)                         */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    const scene_t *s;
+    params_t pr;
+    const double *q;
+    double *val, *grad, *dmin;
+} brute_ctx;
+
+static void brute_one(void *c_, int64_t i, void *scratch)
+{
+    brute_ctx *c = (brute_ctx *)c_;
+    const scene_t *s = c->s;
+    term_t *T = (term_t *)scratch;
+    const double *q = c->q + 3 * i;
+    double dm = INFINITY;
+    for (int64_t k = 0; k < s->n; ++k) {
+        near_t nr;
+        T[k] = prim_term(s, &s->P[k], q, &c->pr, &nr, NULL, NULL);
+        if (nr.d < dm) dm = nr.d;
+    }
+    lse_finish(T, s->n, c->pr.alpha, &c->val[i], &c->grad[3 * i]);
+    if (c->dmin) c->dmin[i] = dm;
+}
+
+void orc_brute(void *h, double alpha, double alpha_u, int paper_metric,
+               const double *q, int64_t m, double *val, double *grad, double *dmin, int nthreads)
+{
+    scene_t *s = (scene_t *)h;
+    brute_ctx c = {s, {alpha, alpha / (alpha > alpha_u ? alpha : alpha_u), paper_metric}, q, val, grad, dmin};
+    run_pool(brute_one, &c, m, sizeof(term_t) * (size_t)(s->n ? s->n : 1), nthreads);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Morton codes and the binary radix tree                                   */
+/* ------------------------------------------------------------------------ */
+/* fp32 centroid in a fixed operation order (no contraction) */
+static void centroid_f(const scene_t *s, const prim_t *p, float *c)
+{
+    const float *V = s->Vf;
+    if (p->kind == K_POINT) {
+        for (int j = 0; j < 3; ++j) c[j] = V[3 * p->v[0] + j];
+    } else if (p->kind == K_SEG) {
+        for (int j = 0; j < 3; ++j) c[j] = (V[3 * p->v[0] + j] + V[3 * p->v[1] + j]) * 0.5f;
+    } else {
+        const float third = 1.0f / 3.0f;
+        for (int j = 0; j < 3; ++j) c[j] = ((V[3 * p->v[0] + j] + V[3 * p->v[1] + j]) + V[3 * p->v[2] + j]) * third;
+    }
+}
+
+static uint64_t morton_of(const float *c, const float *lo, const float *hi)
+{
+    uint32_t k[3];
+    for (int j = 0; j < 3; ++j) {
+        float ext = hi[j] - lo[j];
+        float u = 0.0f;
+        if (ext > 0.0f) u = (c[j] - lo[j]) / ext;
+        if (u < 0.0f) u = 0.0f;
+        if (u > 1.0f) u = 1.0f;
+        float f = floorf(u * 2097152.0f);
+        uint32_t v = (uint32_t)f;
+        k[j] = v > 2097151u ? 2097151u : v;
+    }
+    uint64_t code = 0;
+    for (int b = 20; b >= 0; --b) {
+        code = (code << 1) | ((k[0] >> b) & 1u);
+        code = (code << 1) | ((k[1] >> b) & 1u);
+        code = (code << 1) | ((k[2] >> b) & 1u);
+    }
+    return code;
+}
+
+static const scene_t *g_sort_scene;
+static int cmp_sorted(const void *a, const void *b)
+{
+    int64_t i = *(const int64_t *)a, j = *(const int64_t *)b;
+    uint64_t ci = g_sort_scene->codes[i], cj = g_sort_scene->codes[j];
+    if (ci != cj) return ci < cj ? -1 : 1;
+    return i < j ? -1 : (i > j ? 1 : 0);
+}
+
+/* common-prefix length of the augmented keys (64-bit code, 32-bit index) of
+   buckets i and j (each keyed by its first sorted primitive) */
+static int key_prefix(const scene_t *s, int64_t i, int64_t j)
+{
+    int64_t pi = s->sorted[i * s->L], pj = s->sorted[j * s->L];
+    uint64_t a = s->codes[pi], b = s->codes[pj];
+    if (a != b) return __builtin_clzll(a ^ b);
+    uint32_t x = (uint32_t)pi, y = (uint32_t)pj;
+    return 64 + __builtin_clz(x ^ y);   /* buckets are distinct, so x != y */
+}
+
+static void aabb_init(float *lo, float *hi) { for (int j = 0; j < 3; ++j) { lo[j] = INFINITY; hi[j] = -INFINITY; } }
+static void aabb_addp(const scene_t *s, const prim_t *p, float *lo, float *hi)
+{
+    int nvtx = p->kind == K_POINT ? 1 : (p->kind == K_SEG ? 2 : 3);
+    for (int a = 0; a < nvtx; ++a)
+        for (int j = 0; j < 3; ++j) {
+            float x = s->Vf[3 * p->v[a] + j];
+            if (x < lo[j]) lo[j] = x;
+            if (x > hi[j]) hi[j] = x;
+        }
+}
+
+/* top-down construction of internal node `node` over buckets [first, last] */
+static void build_range(scene_t *s, int64_t node, int64_t first, int64_t last)
+{
+    int dnode = key_prefix(s, first, last);
+    int64_t split = first;
+    for (int64_t i = first; i < last; ++i)
+        if (key_prefix(s, first, i) > dnode) split = i;
+    /* children numbered the Karras way: left = split, right = split + 1 */
+    if (split == first) s->left[node] = -(int32_t)(split + 1);
+    else { s->left[node] = (int32_t)split; build_range(s, split, first, split); }
+    if (split + 1 == last) s->right[node] = -(int32_t)(split + 2);
+    else { s->right[node] = (int32_t)(split + 1); build_range(s, split + 1, split + 1, last); }
+}
+
+static void agg_node(scene_t *s, int32_t child, float *lo, float *hi, int64_t *cnt, int *pts_only);
+static void agg_internal(scene_t *s, int64_t node)
+{
+    float lo[3], hi[3];
+    aabb_init(lo, hi);
+    int64_t cnt = 0; int po = 1;
+    int32_t ch[2] = {s->left[node], s->right[node]};
+    for (int c = 0; c < 2; ++c) {
+        float clo[3], chi[3]; int64_t cc; int cpo;
+        agg_node(s, ch[c], clo, chi, &cc, &cpo);
+        for (int j = 0; j < 3; ++j) { if (clo[j] < lo[j]) lo[j] = clo[j]; if (chi[j] > hi[j]) hi[j] = chi[j]; }
+        cnt += cc; po = po && cpo;
+    }
+    memcpy(s->nlo[node], lo, sizeof(lo)); memcpy(s->nhi[node], hi, sizeof(hi));
+    s->ncount[node] = cnt; s->npts_only[node] = po;
+}
+
+static void agg_node(scene_t *s, int32_t child, float *lo, float *hi, int64_t *cnt, int *pts_only)
+{
+    if (child < 0) {
+        int64_t b = -(int64_t)child - 1;
+        memcpy(lo, s->llo[b], sizeof(float) * 3); memcpy(hi, s->lhi[b], sizeof(float) * 3);
+        *cnt = s->lcount[b]; *pts_only = s->lpts_only[b];
+    } else {
+        agg_internal(s, child);
+        memcpy(lo, s->nlo[child], sizeof(float) * 3); memcpy(hi, s->nhi[child], sizeof(float) * 3);
+        *cnt = s->ncount[child]; *pts_only = s->npts_only[child];
+    }
+}
+
+int orc_tree_build(void *h, int L)
+{
+    scene_t *s = (scene_t *)h;
+    tree_free(s);
+    if (L < 1) return -1;
+    s->L = L;
+    int64_t n = s->n;
+    /* scene box over every vertex */
+    aabb_init(s->slo, s->shi);
+    for (int64_t i = 0; i < s->nv; ++i)
+        for (int j = 0; j < 3; ++j) {
+            float x = s->Vf[3 * i + j];
+            if (x < s->slo[j]) s->slo[j] = x;
+            if (x > s->shi[j]) s->shi[j] = x;
+        }
+    s->codes = (uint64_t *)malloc(sizeof(uint64_t) * (n ? n : 1));
+    s->sorted = (int64_t *)malloc(sizeof(int64_t) * (n ? n : 1));
+    for (int64_t i = 0; i < n; ++i) {
+        float c[3];
+        centroid_f(s, &s->P[i], c);
+        s->codes[i] = morton_of(c, s->slo, s->shi);
+        s->sorted[i] = i;
+    }
+    g_sort_scene = s;
+    qsort(s->sorted, (size_t)n, sizeof(int64_t), cmp_sorted);
+    if (n == 0) { s->nb = 0; return 0; }
+    int64_t nb = (n + L - 1) / L;
+    s->nb = nb;
+    s->llo = malloc(sizeof(float) * 3 * nb); s->lhi = malloc(sizeof(float) * 3 * nb);
+    s->lcount = malloc(sizeof(int64_t) * nb); s->lpts_only = malloc(sizeof(int) * nb);
+    for (int64_t b = 0; b < nb; ++b) {
+        aabb_init(s->llo[b], s->lhi[b]);
+        int64_t e = (b + 1) * L < n ? (b + 1) * L : n;
+        int po = 1;
+        for (int64_t k = b * L; k < e; ++k) {
+            const prim_t *p = &s->P[s->sorted[k]];
+            aabb_addp(s, p, s->llo[b], s->lhi[b]);
+            if (p->kind != K_POINT) po = 0;
+        }
+        s->lcount[b] = e - b * L; s->lpts_only[b] = po;
+    }
+    int64_t ni = nb - 1;
+    int64_t na = ni ? ni : 1;
+    s->left = malloc(sizeof(int32_t) * na); s->right = malloc(sizeof(int32_t) * na);
+    s->nlo = malloc(sizeof(float) * 3 * na); s->nhi = malloc(sizeof(float) * 3 * na);
+    s->ncount = malloc(sizeof(int64_t) * na); s->npts_only = malloc(sizeof(int) * na);
+    if (ni > 0) {
+        build_range(s, 0, 0, nb - 1);
+        agg_internal(s, 0);
+    }
+    return 0;
+}
+
+int64_t orc_tree_nb(void *h) { return ((scene_t *)h)->nb; }
+
+void orc_tree_export(void *h, uint64_t *codes, int64_t *sorted, int32_t *left, int32_t *right,
+                     float *nlo, float *nhi, int64_t *ncount, float *llo, float *lhi, int64_t *lcount,
+                     float *scene_box)
+{
+    scene_t *s = (scene_t *)h;
+    int64_t nb = s->nb, ni = nb > 0 ? nb - 1 : 0;
+    memcpy(codes, s->codes, sizeof(uint64_t) * s->n);
+    memcpy(sorted, s->sorted, sizeof(int64_t) * s->n);
+    if (ni) {
+        memcpy(left, s->left, sizeof(int32_t) * ni); memcpy(right, s->right, sizeof(int32_t) * ni);
+        memcpy(nlo, s->nlo, sizeof(float) * 3 * ni); memcpy(nhi, s->nhi, sizeof(float) * 3 * ni);
+        memcpy(ncount, s->ncount, sizeof(int64_t) * ni);
+    }
+    if (nb) {
+        memcpy(llo, s->llo, sizeof(float) * 3 * nb); memcpy(lhi, s->lhi, sizeof(float) * 3 * nb);
+        memcpy(lcount, s->lcount, sizeof(int64_t) * nb);
+    }
+    for (int j = 0; j < 3; ++j) { scene_box[j] = s->slo[j]; scene_box[3 + j] = s->shi[j]; }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Barnes-Hut (Alg. 1 / Alg. 2, App. D)                                     */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    const scene_t *s;
+    params_t pr;
+    double beta;
+    float beta2f;
+    int decision;          /* 0: fp32 squared test, 1: fp64 ratio test */
+    double wfar;           /* max(A_E, A_T)^S */
+    const double *q;
+    double *val, *grad;
+    int64_t *counts;       /* [m, 3]: nodes tested, far-field accepts, leaf primitives */
+    double *margin;        /* min over tested nodes of |ratio - beta| / beta */
+} bh_ctx;
+
+typedef struct { term_t *T; int64_t n, cap; int64_t tested, far, leafp; double margin; } acc_t;
+
+static void acc_push(acc_t *a, term_t t)
+{
+    if (a->n == a->cap) {
+        a->cap = a->cap ? 2 * a->cap : 256;
+        a->T = (term_t *)realloc(a->T, sizeof(term_t) * a->cap);
+    }
+    a->T[a->n++] = t;
+}
+
+/* The Barnes-Hut condition |B| / d(y_B, q) < beta with y_B the closest point
+   of the box (Sec. 3.5, App. D). Decision mode 0 takes it in FP32 as
+   diag^2 < beta^2 * dbox^2 with the operation order fixed below; mode 1 in
+   FP64 as the ratio. A query inside the box (d = 0) always opens it. */
+static int bh_condition(const bh_ctx *c, const float *lo, const float *hi, const double *q, double *margin)
+{
+    if (c->decision == 0) {
+        float qf[3] = {(float)q[0], (float)q[1], (float)q[2]};
+        float dx[3], ex[3];
+        for (int j = 0; j < 3; ++j) {
+            float a = lo[j] - qf[j], b = qf[j] - hi[j];
+            float m = a > b ? a : b;
+            dx[j] = m > 0.0f ? m : 0.0f;
+            ex[j] = hi[j] - lo[j];
+        }
+        float x0 = dx[0] * dx[0], x1 = dx[1] * dx[1], x2 = dx[2] * dx[2];
+        float dbox2 = (x0 + x1) + x2;
+        float y0 = ex[0] * ex[0], y1 = ex[1] * ex[1], y2 = ex[2] * ex[2];
+        float diag2 = (y0 + y1) + y2;
+        float rhs = c->beta2f * dbox2;
+        if (margin && dbox2 > 0.0f) {
+            double r = sqrt((double)diag2) / sqrt((double)dbox2);
+            double mg = fabs(r - c->beta) / (c->beta > 0 ? c->beta : 1.0);
+            if (mg < *margin) *margin = mg;
+        }
+        return diag2 < rhs;
+    } else {
+        double d2 = 0.0, g2 = 0.0;
+        for (int j = 0; j < 3; ++j) {
+            double l = lo[j], h = hi[j];
+            double y = q[j] < l ? l : (q[j] > h ? h : q[j]);
+            d2 += (q[j] - y) * (q[j] - y);
+            g2 += (h - l) * (h - l);
+        }
+        if (d2 <= 0.0) return 0;
+        double r = sqrt(g2) / sqrt(d2);
+        if (margin) {
+            double mg = fabs(r - c->beta) / (c->beta > 0 ? c->beta : 1.0);
+            if (mg < *margin) *margin = mg;
+        }
+        return r < c->beta;
+    }
+}
+
+static void far_term(const bh_ctx *c, const float *lo, const float *hi, int64_t nB, int pts_only,
+                     const double *q, acc_t *a)
+{
+    double y[3], dv[3];
+    for (int j = 0; j < 3; ++j) {
+        double l = lo[j], h = hi[j];
+        y[j] = q[j] < l ? l : (q[j] > h ? h : q[j]);
+        dv[j] = q[j] - y[j];
+    }
+    double d = sqrt(dot3(dv, dv));
+    double wB = pts_only ? 1.0 : c->wfar;
+    term_t t;
+    t.t = log((double)nB * wB) - c->pr.alpha * d;
+    for (int j = 0; j < 3; ++j) t.v[j] = dv[j] / d;
+    acc_push(a, t);
+}
+
+/* Alg. 1, recursive: the Barnes-Hut test first (also at leaves), else exact
+   leaf terms, else both children. */
+static void collect(const bh_ctx *c, int32_t node, int is_leaf, const double *q, acc_t *a)
+{
+    const scene_t *s = c->s;
+    const float *lo, *hi; int64_t nB; int po;
+    if (is_leaf) { lo = s->llo[node]; hi = s->lhi[node]; nB = s->lcount[node]; po = s->lpts_only[node]; }
+    else { lo = s->nlo[node]; hi = s->nhi[node]; nB = s->ncount[node]; po = s->npts_only[node]; }
+    a->tested++;
+    if (bh_condition(c, lo, hi, q, c->margin ? &a->margin : NULL)) {
+        a->far++;
+        far_term(c, lo, hi, nB, po, q, a);
+        return;
+    }
+    if (is_leaf) {
+        int64_t e = ((int64_t)node + 1) * s->L < s->n ? ((int64_t)node + 1) * s->L : s->n;
+        for (int64_t k = (int64_t)node * s->L; k < e; ++k) {
+            acc_push(a, prim_term(s, &s->P[s->sorted[k]], q, &c->pr, NULL, NULL, NULL));
+            a->leafp++;
+        }
+        return;
+    }
+    int32_t ch[2] = {s->left[node], s->right[node]};
+    for (int k = 0; k < 2; ++k) {
+        if (ch[k] < 0) collect(c, -ch[k] - 1, 1, q, a);
+        else collect(c, ch[k], 0, q, a);
+    }
+}
+
+static void bh_one(void *c_, int64_t i, void *scratch)
+{
+    bh_ctx *c = (bh_ctx *)c_;
+    acc_t *a = (acc_t *)scratch;
+    a->n = 0; a->tested = a->far = a->leafp = 0; a->margin = INFINITY;
+    const double *q = c->q + 3 * i;
+    if (c->s->nb == 1) collect(c, 0, 1, q, a);
+    else if (c->s->nb > 1) collect(c, 0, 0, q, a);
+    lse_finish(a->T, a->n, c->pr.alpha, &c->val[i], &c->grad[3 * i]);
+    if (c->counts) { c->counts[3 * i] = a->tested; c->counts[3 * i + 1] = a->far; c->counts[3 * i + 2] = a->leafp; }
+    if (c->margin) c->margin[i] = a->margin;
+}
+
+typedef struct { bh_ctx *c; int64_t m, next; pthread_mutex_t mu; } bh_pool_t;
+
+static void *bh_worker(void *arg)
+{
+    bh_pool_t *p = (bh_pool_t *)arg;
+    acc_t a; memset(&a, 0, sizeof(a));
+    for (;;) {
+        pthread_mutex_lock(&p->mu);
+        int64_t i0 = p->next; p->next += 16;
+        pthread_mutex_unlock(&p->mu);
+        if (i0 >= p->m) break;
+        int64_t i1 = i0 + 16 < p->m ? i0 + 16 : p->m;
+        for (int64_t i = i0; i < i1; ++i) bh_one(p->c, i, &a);
+    }
+    free(a.T);
+    return NULL;
+}
+
+int orc_bh(void *h, double alpha, double alpha_u, double beta, int paper_metric, int decision,
+           const double *q, int64_t m, double *val, double *grad, int64_t *counts, double *margin, int nthreads)
+{
+    scene_t *s = (scene_t *)h;
+    if (s->n > 0 && s->nb == 0) return -1;
+    bh_ctx c;
+    memset(&c, 0, sizeof(c));
+    c.s = s;
+    c.pr.alpha = alpha;
+    c.pr.S = alpha / (alpha > alpha_u ? alpha : alpha_u);
+    c.pr.paper_metric = paper_metric;
+    c.beta = beta;
+    { float bf = (float)beta; c.beta2f = bf * bf; }
+    c.decision = decision;
+    double A = s->A_E > s->A_T ? s->A_E : s->A_T;
+    c.wfar = pow(A, c.pr.S);
+    c.q = q; c.val = val; c.grad = grad; c.counts = counts; c.margin = margin;
+    bh_pool_t p; p.c = &c; p.m = m; p.next = 0;
+    pthread_mutex_init(&p.mu, NULL);
+    if (nthreads < 1) nthreads = 1;
+    pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * nthreads);
+    for (int t = 0; t < nthreads; ++t) pthread_create(&th[t], NULL, bh_worker, &p);
+    for (int t = 0; t < nthreads; ++t) pthread_join(th[t], NULL);
+    free(th);
+    pthread_mutex_destroy(&p.mu);
+    return 0;
+}
