@@ -1,0 +1,366 @@
+#!/usr/bin/env python
+"""Throughput of the Barnes-Hut smooth distance + gradient (queries/s).
+
+Workload: level-6 icosphere (81,920 triangles, radial noise 0.01), 262,144
+queries (70 % in the shell |r-1| < 0.1, 30 % uniform in [-2,2]^3),
+alpha = 200, beta = 0.5, leaf size 1, paper weights, fp32. One step is the
+whole path: sd_build (validation, valences, Morton codes, radix sort, radix
+tree, aggregates, gather), sd_query_order and sd_query (traversal with the
+fused value + gradient) over one batch resident in HBM. The L2 is flushed
+(a 256 MiB write) before every timed step; the flush is outside the step.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs under torchrun, one rank per GPU: every rank builds the same tree
+and evaluates its own 262,144 queries (weak scaling, no data-path
+collective); the time is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+
+METRIC = "smooth-distance+grad queries/sec (BH)"
+UNIT = "queries/s"
+ALPHA, BETA, LEAF = 200.0, 0.5, 1
+M_QUERIES = 262144
+
+# FP32 operations per unit of Barnes-Hut work in the traversal kernel, hand
+# counted from its source (add/sub/mul/min/max = 1, FMA = 2; MUFU ops and
+# comparisons/selects not counted): one Barnes-Hut test of a child box, the
+# extra work of an accepted far-field node, and one exact triangle term
+# (closest point, degree-7 weight by de Casteljau and its gradient, LSE
+# update). The derivation is in the design doc.
+FLOPS_TEST = 26
+FLOPS_FAR = 26
+FLOPS_TRI = 737
+# FP32 peak: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz maximum SM clock
+SMS, LANES, SM_MAX_GHZ = 152, 128, 2.07
+FP32_PEAK_TFLOPS = SMS * LANES * 2 * SM_MAX_GHZ / 1e3
+
+
+def _args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=100)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--alpha", type=float, default=ALPHA)
+    p.add_argument("--beta", type=float, default=BETA)
+    p.add_argument("--leaf-size", type=int, default=LEAF)
+    p.add_argument("--queries", type=int, default=M_QUERIES)
+    p.add_argument("--no-extras", action="store_true", help="skip plain/e2e/cpu baseline legs")
+    return p.parse_args()
+
+
+def _workload(args, rank=0):
+    c = synth.config2(seed=1, m=args.queries)
+    if rank:
+        c["queries"] = synth.shell_queries(args.queries, 0.7, 0.9, 1.1, 2.0, seed=101 + rank)
+    return c
+
+
+def _config(args, n):
+    return {"workload": f"icosphere-L6 81920 tris, {args.queries} queries/GPU (70% shell, 30% box), "
+                        f"alpha={args.alpha:g}, beta={args.beta:g}, leaf={args.leaf_size}",
+            "triangles": 81920, "queries_per_gpu": args.queries, "alpha": args.alpha, "beta": args.beta,
+            "leaf_size": args.leaf_size, "step": "sd_build + sd_query_order + sd_query (value+grad)",
+            "l2": "flushed (256 MiB write) before each timed step", "parallelism": f"replicated tree, dp{n}"}
+
+
+def _src_hash():
+    h = hashlib.sha256()
+    for f in ("sd_query.cu", "sd_common.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2108_10480_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def _traffic(kernel_hash):
+    """Per-launch DRAM bytes of the traversal kernel from the committed ncu
+    summary, or None if the kernel changed since it was captured."""
+    path = os.path.join(ROOT, "profiles", "k_traverse_ico6_traffic.json")
+    try:
+        d = json.load(open(path))
+    except Exception:
+        return None
+    if d.get("src_hash") != kernel_hash:
+        return None
+    return d.get("dram_bytes_per_launch")
+
+
+class _Clocks:
+    def __init__(self, index):
+        self.p = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(
+                ["nvidia-smi", "-i", str(index), "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,"
+                 "clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+                 "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2108_10480_gb300 import SmoothDistance, kernel_launches
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    c = _workload(args, rank)
+    V = torch.from_numpy(c["V"]).to(dev)
+    F = torch.from_numpy(c["F"]).to(dev)
+    q = torch.from_numpy(c["queries"]).to(dev)
+    M = q.shape[0]
+    val = torch.empty(M, device=dev)
+    grad = torch.empty(M, 3, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(evs=None):
+        if evs:
+            evs[0].record(stream)
+        sd = SmoothDistance(tris=(V, F), alpha=args.alpha, beta=args.beta, leaf_size=args.leaf_size, device=dev)
+        order = sd.query_order(q)
+        if evs:
+            evs[1].record(stream)
+        sd.query(q, out=(val, grad), order=order)
+        if evs:
+            evs[2].record(stream)
+        return sd
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    # work counts of this workload (decisions are deterministic)
+    sd = step()
+    _, _, cnt = sd.query(q, counts=True)
+    tot = cnt.to(torch.int64).sum(0).tolist()
+    del sd
+    clocks = _Clocks(local) if rank == 0 else None
+    barrier()
+    launches0 = kernel_launches()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    t_wall = time.perf_counter()
+    for k in range(args.steps):
+        flush.fill_(k & 255)
+        step(evs[k])
+    barrier()
+    t_wall = time.perf_counter() - t_wall
+    launches = kernel_launches() - launches0
+    clk = clocks.stop() if clocks else None
+    step_ms = [e[0].elapsed_time(e[2]) for e in evs]
+    trav_ms = [e[1].elapsed_time(e[2]) for e in evs]
+    build_ms = [e[0].elapsed_time(e[1]) for e in evs]
+    ms = sum(step_ms) / len(step_ms)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * M / (ms / 1e3)
+
+    out = None
+    if rank == 0:
+        trav = statistics.mean(trav_ms)
+        flops = tot[0] * FLOPS_TEST + tot[1] * FLOPS_FAR + tot[2] * FLOPS_TRI
+        achieved = flops / (trav / 1e3) / 1e12
+        kh = _src_hash()
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded generators, synth/)",
+            "config": _config(args, world),
+            "breakdown_ms": {"build_and_order": statistics.mean(build_ms), "traverse": trav},
+            "work": {"bh_tests": tot[0], "far_accepts": tot[1], "leaf_triangles": tot[2],
+                     "per_query": [x / M for x in tot]},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": achieved / FP32_PEAK_TFLOPS, "traffic": _traffic(kh),
+                         "kernel": "k_traverse<tris,grad>", "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
+                         "kernel_src_hash": kh},
+            "gpu_launches": launches,
+            "wall_s_timed": t_wall,
+        }
+        if clk:
+            out["clocks"] = clk
+        if not args.no_extras:
+            out.update(_extras(args, c, V, F, q, dev, M))
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return out
+
+
+def _extras(args, c, V, F, q, dev, M):
+    """plain GPU brute force, end-to-end through host buffers, CPU oracle."""
+    import torch
+
+    from paper_2108_10480_gb300 import SmoothDistance
+    res = {}
+    stream = torch.cuda.current_stream()
+    # plain method (all pairs) on the same queries
+    sd = SmoothDistance(tris=(V, F), alpha=args.alpha, beta=args.beta, leaf_size=args.leaf_size, device=dev)
+    vb = torch.empty(M, device=dev)
+    gb = torch.empty(M, 3, device=dev)
+    sd.query_brute(q, out=(vb, gb))
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sd.query_brute(q, out=(vb, gb))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    tb = e0.elapsed_time(e1)
+    res["plain"] = {"value": M / (tb / 1e3), "unit": UNIT, "ms": tb, "what": "sd_query_brute, all pairs"}
+    del sd
+    # end to end: pinned host inputs -> device, build + order + query, result -> pinned host
+    hV = torch.from_numpy(c["V"]).pin_memory()
+    hF = torch.from_numpy(c["F"]).pin_memory()
+    hq = torch.from_numpy(c["queries"]).pin_memory()
+    hv = torch.empty(M).pin_memory()
+    hg = torch.empty(M, 3).pin_memory()
+    dV, dF, dq = torch.empty_like(V), torch.empty_like(F), torch.empty_like(q)
+    dv, dg = torch.empty(M, device=dev), torch.empty(M, 3, device=dev)
+
+    def e2e_step():
+        dV.copy_(hV, non_blocking=True)
+        dF.copy_(hF, non_blocking=True)
+        dq.copy_(hq, non_blocking=True)
+        s = SmoothDistance(tris=(dV, dF), alpha=args.alpha, beta=args.beta, leaf_size=args.leaf_size, device=dev)
+        s.query(dq, out=(dv, dg))
+        hv.copy_(dv, non_blocking=True)
+        hg.copy_(dg, non_blocking=True)
+
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize()
+    n = max(3, args.steps)
+    e0.record(stream)
+    for _ in range(n):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    te = e0.elapsed_time(e1) / n
+    res["e2e"] = {"value": M / (te / 1e3), "unit": UNIT, "ms_per_step": te,
+                  "h2d_bytes_per_step": int(hV.numel() * 4 + hF.numel() * 4 + hq.numel() * 4),
+                  "d2h_bytes_per_step": int(hv.numel() * 4 + hg.numel() * 4)}
+    res["cpu_baseline"] = _cpu_baseline(c, args)
+    return res
+
+
+def _cpu_baseline(c, args, sample=None):
+    """The FP64 oracle as it stands on this host's cores: its own tree build
+    over the full mesh plus Barnes-Hut on a query sample; the rate is scaled
+    to the full batch as M / (t_build + t_query * M / sample)."""
+    import oracle
+    cores = oracle.default_threads()
+    M = c["queries"].shape[0]
+    if sample is None:
+        sample = min(M, 8192 * max(1, cores // 2))
+    qs = c["queries"][:sample]
+    t0 = time.perf_counter()
+    sc = oracle.Scene(tri_V=c["V"], tri_F=c["F"])
+    sc.build_tree(args.leaf_size)
+    t1 = time.perf_counter()
+    sc.bh(qs, args.alpha, args.beta, threads=cores)
+    t2 = time.perf_counter()
+    tb, tq = t1 - t0, t2 - t1
+    full = tb + tq * M / sample
+    return {"value": M / full, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"oracle tree build over all 81,920 triangles ({tb:.2f} s) + FP64 Barnes-Hut on the first "
+                      f"{sample} of {M} queries ({tq:.2f} s, {cores} threads); rate scaled to the full batch"}
+
+
+def run_reference(args):
+    """Reference arm: the FP64 oracle on the host cores, each step a bounded
+    sample of the same workload."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return None
+    import oracle
+    c = _workload(args, 0)
+    cores = oracle.default_threads()
+    M = c["queries"].shape[0]
+    sample = min(M, 4096 * cores)
+    times = []
+    for k in range(args.warmup + args.steps):
+        r = _cpu_baseline(c, args, sample=sample)
+        if k >= args.warmup:
+            times.append(M / r["value"])
+    ms = 1e3 * sum(times) / len(times)
+    value = M / (ms / 1e3)
+    return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded generators, synth/)",
+            "config": _config(args, 1), "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"per step: oracle tree build + Barnes-Hut on {sample} of {M} queries, "
+                                       f"scaled to the full batch"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = _args()
+    out = run_reference(args) if args.impl == "reference" else run_ours(args)
+    if out is not None:
+        print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,187 @@
+/*
+ * libsd: smooth distance and gradient on co-dimensional geometry, on one GPU.
+ *
+ * Computes, for a batch of query points q, the weighted LogSumExp smooth
+ * minimum distance of Madan & Levin ("Fast Evaluation of Smooth Distance
+ * Constraints on Co-Dimensional Geometry"), Eq. 3,
+ *
+ *     d^(q) = -(1/alpha) log sum_i w_i(q) exp(-alpha d_i(q)),
+ *
+ * and its gradient, Eq. 4, over a data mesh of points, edges and triangles,
+ * with the blending weights of Sec. 3.3 / App. C and the conservative
+ * Barnes-Hut far field of Sec. 3.5 / App. D (Alg. 1 and Alg. 2).
+ *
+ * Conventions for every entry point:
+ *   - Returns an sd_status (SD_OK == 0); nothing is thrown across the ABI.
+ *   - "device" pointers are CUDA device memory of the current device; the
+ *     caller owns them and keeps them alive until the work on `stream` ends.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default).
+ *   - Arrays are row-major, contiguous: xyz triples are [n,3] float32,
+ *     index tuples are [m,2] / [m,3] int32 (0-based into their own vertex
+ *     array).
+ */
+#ifndef SD_H_
+#define SD_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SD_OK = 0,
+    SD_ERR_INVALID_ARG = 1, /* bad pointer/size/parameter; nothing was launched */
+    SD_ERR_CUDA = 2,        /* a CUDA call failed (the library's last error text is kept) */
+    SD_ERR_OOM = 3,         /* device allocation failed */
+    SD_ERR_NONFINITE = 4,   /* a vertex or query coordinate is NaN/Inf */
+    SD_ERR_INDEX = 5,       /* an edge/triangle index is outside its vertex array */
+    SD_ERR_TOO_LARGE = 6    /* a size exceeds what the library supports (2^31-1 primitives) */
+} sd_status;
+
+/* Geometry of the data mesh M_d = (V, F) (Sec. 3). Each part may be empty
+   (count 0, pointer ignored). Primitive order: points, then edges, then
+   triangles; "original index" below means this order. */
+typedef struct { const float* xyz; int64_t n; } sd_points;                              /* device [n,3] */
+typedef struct { const float* V; int64_t nv; const int32_t* E; int64_t ne; } sd_edges;   /* device [nv,3], [ne,2] */
+typedef struct { const float* V; int64_t nv; const int32_t* F; int64_t nf; } sd_tris;    /* device [nv,3], [nf,3] */
+typedef struct { sd_points pts; sd_edges edges; sd_tris tris; } sd_geometry;
+
+enum { SD_WEIGHTS_PAPER = 0, SD_WEIGHTS_UNIT = 1 };
+
+typedef struct {
+    float alpha_u;        /* attenuation threshold alpha_U of Sec. 3.3: S = alpha / max(alpha, alpha_U); 0 => S = 1 */
+    int32_t leaf_size;    /* L >= 1: primitives per leaf bucket (part of the tree's definition; the paper uses 1) */
+    int32_t weights;      /* SD_WEIGHTS_PAPER: w_i = (A w~_i)^S of App. C; SD_WEIGHTS_UNIT: w_i = 1 */
+    int32_t paper_metric; /* 1: barycentric gradients measured in the alpha-scaled metric of Sec. 3.3
+                             (the weight-gradient term is divided by alpha once more); 0: exact gradient */
+} sd_build_opts;
+
+typedef struct {
+    int32_t sort_queries; /* 1 (default): traverse in Morton order of the queries (results are unchanged) */
+    int32_t block;        /* threads per block of the traversal kernel: a multiple of 32 up to 256;
+                             0 = library default (128) */
+    int32_t* counts;      /* optional device [M,3] int32 output: Barnes-Hut tests, far-field accepts,
+                             leaf primitives evaluated (the work counts of Alg. 1), or NULL */
+    const int32_t* order; /* optional device [M] permutation of 0..M-1 giving the traversal order (as
+                             written by sd_query_order); when set, sort_queries is ignored */
+} sd_query_opts;
+
+typedef struct sd_tree sd_tree;
+
+/* Fill option structs with defaults (alpha_u 0, L 1, paper weights, exact
+   metric; sorted queries, default block, no counts). */
+void sd_default_build_opts(sd_build_opts* o);
+void sd_default_query_opts(sd_query_opts* o);
+
+/*
+ * Build the acceleration structure for Alg. 1 (Sec. 3.5, App. D) on `stream`:
+ * validation, incidence counts and weight parameters (App. C.2-C.3), 63-bit
+ * Morton codes, a stable radix sort by (code, original index), a binary
+ * radix tree over leaf buckets of L consecutive sorted primitives, per-node
+ * AABBs, primitive counts n_B and far-field weights w_B (App. D), and the
+ * primitives re-packed in leaf order.
+ *   g      host pointer to the geometry (its arrays are device pointers)
+ *   alpha  > 0, accuracy parameter of Eq. 3
+ *   beta   >= 0, Barnes-Hut parameter (0 = exact evaluation, Sec. 3.5)
+ *   opts   host pointer or NULL for defaults
+ *   out    receives the new tree; the tree owns copies of everything it
+ *          needs, so `g`'s arrays may be freed after the call returns.
+ * Synchronises `stream` before returning (it reports data errors such as
+ * SD_ERR_NONFINITE / SD_ERR_INDEX, in which case *out is NULL).
+ */
+int sd_build(const sd_geometry* g, float alpha, float beta, const sd_build_opts* opts,
+             void* stream, sd_tree** out);
+
+/*
+ * Barnes-Hut smooth distance and gradient (Alg. 2 over Alg. 1) at M queries.
+ *   q      device [M,3] float32 query points
+ *   value  device [M] float32 output d^(q); +inf for an empty data mesh
+ *   grad   device [M,3] float32 output grad d^(q), or NULL for value only
+ *   opts   host pointer or NULL for defaults
+ * Asynchronous on `stream`. A non-finite query yields NaN outputs for that
+ * query and sets the tree's status word to SD_ERR_NONFINITE (read it with
+ * sd_query_status). Concurrent calls on one tree are safe; they share only
+ * the status word.
+ */
+int sd_query(const sd_tree* t, const float* q, int64_t M, float* value, float* grad,
+             const sd_query_opts* opts, void* stream);
+
+/*
+ * Traversal order for sd_query: writes to `order` (device [M] int32) the
+ * query indices sorted by the 30-bit Morton code of each query relative to
+ * the tree's scene box (stable; ties keep index order). Asynchronous on
+ * `stream`; uses stream-ordered temporary device memory.
+ */
+int sd_query_order(const sd_tree* t, const float* q, int64_t M, int32_t* order, void* stream);
+
+/*
+ * The plain method: Eq. 3 / Eq. 4 summed exactly over every primitive (no
+ * tree pruning; equivalent to beta = 0), with the same weights as `t`.
+ * Same arguments and behaviour as sd_query (opts->counts is ignored).
+ */
+int sd_query_brute(const sd_tree* t, const float* q, int64_t M, float* value, float* grad,
+                   const sd_query_opts* opts, void* stream);
+
+/* Synchronise `stream`, return and clear the tree's device status word. */
+int sd_query_status(const sd_tree* t, void* stream);
+
+typedef struct {
+    int64_t n_prims, n_points, n_edges, n_tris;
+    int64_t n_buckets;   /* leaf buckets nb = ceil(n/L); internal nodes nb - 1 */
+    int32_t leaf_size;
+    float alpha, beta, alpha_u, S;
+    float A_E, A_T;      /* scale A of App. C.2 / C.3 (1 when the part is empty) */
+    float w_far;         /* far-field weight max(A_E, A_T)^S for nodes holding an edge or triangle */
+    float scene_lo[3], scene_hi[3];
+    int64_t device_bytes;
+} sd_tree_info;
+
+int sd_tree_get_info(const sd_tree* t, sd_tree_info* info);
+
+/* Host copies of the build's results, for tests. Every pointer is a host
+   array the caller allocated with the size given (n = n_prims, nb =
+   n_buckets, ni = nb - 1), or NULL to skip it.
+     codes    [n]    uint64 Morton code of each primitive (original order)
+     sorted   [n]    int32 original index of the primitive at each sorted position
+     left/right [ni] int32 children of internal node i (Karras numbering; a
+                     leaf child b is stored as -(b + 1))
+     node_lo/node_hi [ni,3], node_count [ni]   internal node AABB and n_B
+     leaf_lo/leaf_hi [nb,3], leaf_count [nb]   bucket AABB and n_B
+     params   [n,2]  float per-primitive weight parameters in original order:
+                     edges (1/|N_i0|, 1/|N_i1|), triangles (1/v_i, 1/e_i), points (0,0) */
+typedef struct {
+    uint64_t* codes; int32_t* sorted;
+    int32_t* left; int32_t* right;
+    float* node_lo; float* node_hi; int32_t* node_count;
+    float* leaf_lo; float* leaf_hi; int32_t* leaf_count;
+    float* params;
+} sd_tree_view;
+
+int sd_tree_export(const sd_tree* t, sd_tree_view* view);
+
+/* Release the tree (synchronises the device). NULL is a no-op. */
+void sd_free(sd_tree* t);
+
+/* Number of CUDA kernels this library has launched in this process. */
+int64_t sd_kernel_launches(void);
+
+/* Static text for a status code; sd_last_error() holds the last CUDA error
+   text seen by this thread. */
+const char* sd_status_str(int status);
+const char* sd_last_error(void);
+
+/*
+ * Host-only: the library's triangle weight basis (App. C.3) in Bernstein
+ * form. out[3*36]: for unit right-hand sides (1/v, 1/e, (v-1)/v) in that
+ * order, the 36 Bernstein-Bezier coefficients b_ijk of the degree-7
+ * polynomial, (i,j,k) = exponents of (phi0, phi1, phi2), i+j+k = 7, in the
+ * order i = 7..0 outer, j = 7-i..0 inner. Needs no GPU.
+ */
+int sd_weight_basis(double* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SD_H_ */

@@ -69,13 +69,13 @@ def _load():
         lib.orc_scene_info.argtypes = [P, P]
         lib.orc_prim_params.argtypes = [P, P, P, P]
         lib.orc_prim_eval.argtypes = [P, i64, d, d, i, P, P]
-        lib.orc_brute.argtypes = [P, d, d, i, P, i64, P, P, P, i]
+        lib.orc_brute.argtypes = [P, d, d, i, i, P, i64, P, P, P, i]
         lib.orc_tree_build.argtypes = [P, i]
         lib.orc_tree_build.restype = i
         lib.orc_tree_nb.argtypes = [P]
         lib.orc_tree_nb.restype = i64
         lib.orc_tree_export.argtypes = [P] * 12
-        lib.orc_bh.argtypes = [P, d, d, d, i, i, P, i64, P, P, P, P, i]
+        lib.orc_bh.argtypes = [P, d, d, d, i, i, i, P, i64, P, P, P, P, i]
         lib.orc_bh.restype = i
         _lib = lib
         return lib
@@ -102,6 +102,11 @@ class Scene:
         self.points = f32(points)
         self.edge_V, self.edge_E = f32(edge_V), i32(edge_E, 2)
         self.tri_V, self.tri_F = f32(tri_V), i32(tri_F, 3)
+        # a vertex array without primitives does not belong to the data mesh
+        if self.edge_E.shape[0] == 0:
+            self.edge_V = f32(None)
+        if self.tri_F.shape[0] == 0:
+            self.tri_V = f32(None)
         self.ebasis = np.ascontiguousarray(weights.edge_basis(), dtype=np.float64)
         self.tbasis = np.ascontiguousarray(weights.tri_basis(), dtype=np.float64)
         self._h = lib.orc_scene_new(
@@ -140,13 +145,14 @@ class Scene:
                     grad_wt=out[7:10].copy(), t=out[10], vec=out[11:14].copy())
 
     # -- brute force ---------------------------------------------------------
-    def brute(self, q, alpha, alpha_u=0.0, paper_metric=False, threads=None):
+    def brute(self, q, alpha, alpha_u=0.0, paper_metric=False, threads=None, unit=False):
         """Exact d^ and grad d^ over every primitive (Eq. 3, Eq. 4) plus the
-        exact minimum distance d_min (Eq. 2). q: [m,3] (promoted to FP64)."""
+        exact minimum distance d_min (Eq. 2). q: [m,3] (promoted to FP64).
+        unit=True sets every weight to 1 (the plain LogSumExp)."""
         q = np.ascontiguousarray(np.asarray(q, np.float64).reshape(-1, 3))
         m = q.shape[0]
         val = np.zeros(m); grad = np.zeros((m, 3)); dmin = np.zeros(m)
-        _load().orc_brute(self._h, float(alpha), float(alpha_u), int(bool(paper_metric)), _ptr(q), m,
+        _load().orc_brute(self._h, float(alpha), float(alpha_u), int(bool(paper_metric)), int(bool(unit)), _ptr(q), m,
                           _ptr(val), _ptr(grad), _ptr(dmin), int(threads or default_threads()))
         return val, grad, dmin
 
@@ -179,7 +185,7 @@ class Scene:
         return t
 
     def bh(self, q, alpha, beta, alpha_u=0.0, paper_metric=False, decision="fp32",
-           threads=None, want_margin=False):
+           threads=None, want_margin=False, unit=False):
         """Barnes-Hut d^ and grad d^ (Alg. 1, Alg. 2) on this scene's tree.
         decision: "fp32" takes the test |B|^2 < beta^2 d^2 in FP32 in a fixed
         operation order (the precision of the GPU kernels); "fp64" takes
@@ -192,7 +198,7 @@ class Scene:
         val = np.zeros(m); grad = np.zeros((m, 3)); counts = np.zeros((m, 3), np.int64)
         margin = np.zeros(m) if want_margin else None
         rc = _load().orc_bh(self._h, float(alpha), float(alpha_u), float(beta), int(bool(paper_metric)),
-                            0 if decision == "fp32" else 1, _ptr(q), m, _ptr(val), _ptr(grad), _ptr(counts),
+                            int(bool(unit)), 0 if decision == "fp32" else 1, _ptr(q), m, _ptr(val), _ptr(grad), _ptr(counts),
                             _ptr(margin) if margin is not None else ctypes.c_void_p(0),
                             int(threads or default_threads()))
         if rc != 0:

@@ -274,7 +274,8 @@ static void near_triangle(const double *v0, const double *v1, const double *v2, 
     double g00 = dot3(e1, e1), g01 = dot3(e1, e2), g11 = dot3(e2, e2);
     double det = g00 * g11 - g01 * g01;
     double scale = g00 * g11;
-    int degenerate = !(det > 1e-14 * scale) || scale == 0.0;
+    /* sin^2 of the corner angle below 1e-10 counts as zero area */
+    int degenerate = !(det > 1e-10 * scale) || scale == 0.0;
     if (!degenerate) {
         double r0 = dot3(ap, e1), r1 = dot3(ap, e2);
         double p1 = (g11 * r0 - g01 * r1) / det;
@@ -357,6 +358,7 @@ typedef struct { double t; double v[3]; } term_t;
 typedef struct {
     double alpha, S;
     int paper_metric;
+    int unit;          /* unit weights: w_i = 1 for every primitive */
 } params_t;
 
 static void prim_near(const scene_t *s, const prim_t *p, const double *q, near_t *nr)
@@ -381,7 +383,7 @@ static term_t prim_term(const scene_t *s, const prim_t *p, const double *q, cons
         if (pr->paper_metric)
             for (int j = 0; j < 3; ++j) gwt[j] /= pr->alpha;
     }
-    if (p->kind == K_POINT) {
+    if (p->kind == K_POINT || pr->unit) {
         T.t = -pr->alpha * nr.d;
         for (int j = 0; j < 3; ++j) T.v[j] = nr.gd[j];
     } else {
@@ -401,7 +403,7 @@ void orc_prim_eval(void *h, int64_t i, double alpha, double alpha_u, int paper_m
                    const double *q, double *out)
 {
     scene_t *s = (scene_t *)h;
-    params_t pr = {alpha, alpha / (alpha > alpha_u ? alpha : alpha_u), paper_metric};
+    params_t pr = {alpha, alpha / (alpha > alpha_u ? alpha : alpha_u), paper_metric, 0};
     near_t nr; double wt, gwt[3];
     term_t T = prim_term(s, &s->P[i], q, &pr, &nr, &wt, gwt);
     out[0] = nr.d;
@@ -496,11 +498,11 @@ static void brute_one(void *c_, int64_t i, void *scratch)
     if (c->dmin) c->dmin[i] = dm;
 }
 
-void orc_brute(void *h, double alpha, double alpha_u, int paper_metric,
+void orc_brute(void *h, double alpha, double alpha_u, int paper_metric, int unit,
                const double *q, int64_t m, double *val, double *grad, double *dmin, int nthreads)
 {
     scene_t *s = (scene_t *)h;
-    brute_ctx c = {s, {alpha, alpha / (alpha > alpha_u ? alpha : alpha_u), paper_metric}, q, val, grad, dmin};
+    brute_ctx c = {s, {alpha, alpha / (alpha > alpha_u ? alpha : alpha_u), paper_metric, unit}, q, val, grad, dmin};
     run_pool(brute_one, &c, m, sizeof(term_t) * (size_t)(s->n ? s->n : 1), nthreads);
 }
 
@@ -842,7 +844,7 @@ static void *bh_worker(void *arg)
     return NULL;
 }
 
-int orc_bh(void *h, double alpha, double alpha_u, double beta, int paper_metric, int decision,
+int orc_bh(void *h, double alpha, double alpha_u, double beta, int paper_metric, int unit, int decision,
            const double *q, int64_t m, double *val, double *grad, int64_t *counts, double *margin, int nthreads)
 {
     scene_t *s = (scene_t *)h;
@@ -853,11 +855,12 @@ int orc_bh(void *h, double alpha, double alpha_u, double beta, int paper_metric,
     c.pr.alpha = alpha;
     c.pr.S = alpha / (alpha > alpha_u ? alpha : alpha_u);
     c.pr.paper_metric = paper_metric;
+    c.pr.unit = unit;
     c.beta = beta;
     { float bf = (float)beta; c.beta2f = bf * bf; }
     c.decision = decision;
     double A = s->A_E > s->A_T ? s->A_E : s->A_T;
-    c.wfar = pow(A, c.pr.S);
+    c.wfar = unit ? 1.0 : pow(A, c.pr.S);
     c.q = q; c.val = val; c.grad = grad; c.counts = counts; c.margin = margin;
     bh_pool_t p; p.c = &c; p.m = m; p.next = 0;
     pthread_mutex_init(&p.mu, NULL);

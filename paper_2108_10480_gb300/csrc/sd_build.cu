@@ -1,0 +1,694 @@
+// sd_build: the acceleration structure of Alg. 1 (Sec. 3.5, App. D) built on
+// the GPU, plus the per-primitive weight parameters of App. C.
+//
+// Stream order of one build:
+//   validate -> scene box -> incidence counts / weight parameters ->
+//   Morton codes -> radix sort by (code, index) -> radix tree (Karras) ->
+//   bottom-up AABBs, counts and far-field masses -> leaf-order gather.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "sd_common.cuh"
+#include "sd_sort.cuh"
+
+namespace {
+
+enum { ST_NONFINITE = 1, ST_INDEX = 2 };
+
+// scalars the build accumulates on the device
+struct BuildScalars {
+    unsigned box[6];   // scene box as order-preserving unsigned keys: lo.xyz (min), hi.xyz (max)
+    int status;
+    int A_E, A_T;
+    int pad;
+};
+
+__device__ __forceinline__ unsigned f2key(float f)
+{
+    unsigned u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __host__ __forceinline__ float key2f(unsigned k)
+{
+    unsigned u = (k & 0x80000000u) ? (k & 0x7fffffffu) : ~k;
+#ifdef __CUDA_ARCH__
+    return __uint_as_float(u);
+#else
+    float f;
+    std::memcpy(&f, &u, 4);
+    return f;
+#endif
+}
+
+struct Geo {
+    const float* P; int np;
+    const float* EV; int nev; const int* E; int ne;
+    const float* TV; int ntv; const int* F; int nf;
+    int n;
+};
+
+// vertex j (0..2) of primitive i, as fp32 xyz
+__device__ __forceinline__ float3 prim_vertex(const Geo& g, int i, int j)
+{
+    const float* p;
+    if (i < g.np) p = g.P + 3 * i;
+    else if (i < g.np + g.ne) p = g.EV + 3 * g.E[2 * (i - g.np) + j];
+    else p = g.TV + 3 * g.F[3 * (i - g.np - g.ne) + j];
+    return make_float3(p[0], p[1], p[2]);
+}
+__device__ __forceinline__ int prim_nv(const Geo& g, int i) { return i < g.np ? 1 : (i < g.np + g.ne ? 2 : 3); }
+
+// --- validation and scene box --------------------------------------------
+__global__ void k_vertices(const float* __restrict__ x, int nv, BuildScalars* bs)
+{
+    float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    bool bad = false;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += gridDim.x * blockDim.x) {
+        for (int j = 0; j < 3; ++j) {
+            float v = x[3 * i + j];
+            bad |= !isfinite(v);
+            lo[j] = fminf(lo[j], v);
+            hi[j] = fmaxf(hi[j], v);
+        }
+    }
+    if (bad) atomicOr(&bs->status, ST_NONFINITE);
+    for (int j = 0; j < 3; ++j) {
+        for (int o = 16; o > 0; o >>= 1) {
+            lo[j] = fminf(lo[j], __shfl_xor_sync(0xffffffffu, lo[j], o));
+            hi[j] = fmaxf(hi[j], __shfl_xor_sync(0xffffffffu, hi[j], o));
+        }
+    }
+    if ((threadIdx.x & 31) == 0) {
+        for (int j = 0; j < 3; ++j) {
+            if (lo[j] <= hi[j]) {
+                atomicMin(&bs->box[j], f2key(lo[j]));
+                atomicMax(&bs->box[3 + j], f2key(hi[j]));
+            }
+        }
+    }
+}
+
+__global__ void k_check_index(const int* __restrict__ idx, int64_t count, int nv, BuildScalars* bs)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+        int v = idx[i];
+        if (v < 0 || v >= nv) atomicOr(&bs->status, ST_INDEX);
+    }
+}
+
+// --- incidence counts (App. C.2, C.3): one count per incidence slot -------
+__global__ void k_count_slots(const int* __restrict__ idx, int64_t count, int* __restrict__ cnt)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(&cnt[idx[i]], 1);
+}
+
+__device__ __forceinline__ unsigned long long edge_key(int a, int b)
+{
+    unsigned lo = (unsigned)min(a, b), hi = (unsigned)max(a, b);
+    return ((unsigned long long)lo << 32) | hi;
+}
+__device__ __forceinline__ unsigned hash64(unsigned long long k, unsigned mask)
+{
+    k ^= k >> 33; k *= 0xff51afd7ed558ccdull; k ^= k >> 33; k *= 0xc4ceb9fe1a85ec53ull; k ^= k >> 33;
+    return (unsigned)k & mask;
+}
+
+// open-addressing table: key per slot, count per slot; probing is bounded by
+// the capacity (load factor <= 1/2, so a slot is always found)
+__global__ void k_edge_insert(const int* __restrict__ F, int nf, unsigned long long* keys, int* counts, unsigned mask)
+{
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= 3 * nf) return;
+    int t = s / 3, j = s - 3 * t;
+    unsigned long long k = edge_key(F[3 * t + j], F[3 * t + (j + 1) % 3]);
+    unsigned h = hash64(k, mask);
+    for (unsigned probe = 0; probe <= mask; ++probe) {
+        unsigned long long prev = atomicCAS(&keys[h], ~0ull, k);
+        if (prev == ~0ull || prev == k) { atomicAdd(&counts[h], 1); return; }
+        h = (h + 1) & mask;
+    }
+}
+
+__device__ __forceinline__ int edge_lookup(const unsigned long long* keys, const int* counts, unsigned mask,
+                                           unsigned long long k)
+{
+    unsigned h = hash64(k, mask);
+    for (unsigned probe = 0; probe <= mask; ++probe) {
+        unsigned long long v = keys[h];
+        if (v == k) return counts[h];
+        if (v == ~0ull) return 0;
+        h = (h + 1) & mask;
+    }
+    return 0;
+}
+
+// triangle i: v_i = max vertex valence, e_i = max edge valence -> (1/v_i, 1/e_i)
+__global__ void k_tri_params(const int* __restrict__ F, int nf, const int* __restrict__ vcnt,
+                             const unsigned long long* keys, const int* counts, unsigned mask,
+                             float* __restrict__ params, int first, BuildScalars* bs)
+{
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nf) return;
+    int a = F[3 * t], b = F[3 * t + 1], c = F[3 * t + 2];
+    int vm = max(vcnt[a], max(vcnt[b], vcnt[c]));
+    int em = max(edge_lookup(keys, counts, mask, edge_key(a, b)),
+                 max(edge_lookup(keys, counts, mask, edge_key(b, c)), edge_lookup(keys, counts, mask, edge_key(c, a))));
+    params[2 * (first + t)] = 1.f / (float)vm;
+    params[2 * (first + t) + 1] = 1.f / (float)max(em, 1);
+    atomicMax(&bs->A_T, vm);
+}
+
+// edge i: (u, v) = (1/|N_i0|, 1/|N_i1|)
+__global__ void k_edge_params(const int* __restrict__ E, int ne, const int* __restrict__ cnt,
+                              float* __restrict__ params, int first, BuildScalars* bs)
+{
+    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= ne) return;
+    int c0 = cnt[E[2 * e]], c1 = cnt[E[2 * e + 1]];
+    params[2 * (first + e)] = 1.f / (float)c0;
+    params[2 * (first + e) + 1] = 1.f / (float)c1;
+    atomicMax(&bs->A_E, max(c0, c1));
+}
+
+// --- Morton codes (fp32 centroid in a fixed operation order) ---------------
+__global__ void k_morton(Geo g, const BuildScalars* bs, unsigned long long* __restrict__ codes,
+                         unsigned long long* __restrict__ keys, int* __restrict__ vals)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.n) return;
+    float lo[3], hi[3];
+    for (int j = 0; j < 3; ++j) { lo[j] = key2f(bs->box[j]); hi[j] = key2f(bs->box[3 + j]); }
+    int nvx = prim_nv(g, i);
+    float3 a = prim_vertex(g, i, 0);
+    float c[3] = {a.x, a.y, a.z};
+    if (nvx == 2) {
+        float3 b = prim_vertex(g, i, 1);
+        c[0] = __fmul_rn(__fadd_rn(a.x, b.x), 0.5f);
+        c[1] = __fmul_rn(__fadd_rn(a.y, b.y), 0.5f);
+        c[2] = __fmul_rn(__fadd_rn(a.z, b.z), 0.5f);
+    } else if (nvx == 3) {
+        float3 b = prim_vertex(g, i, 1), d = prim_vertex(g, i, 2);
+        const float third = 1.0f / 3.0f;
+        c[0] = __fmul_rn(__fadd_rn(__fadd_rn(a.x, b.x), d.x), third);
+        c[1] = __fmul_rn(__fadd_rn(__fadd_rn(a.y, b.y), d.y), third);
+        c[2] = __fmul_rn(__fadd_rn(__fadd_rn(a.z, b.z), d.z), third);
+    }
+    unsigned k[3];
+    for (int j = 0; j < 3; ++j) {
+        float ext = __fsub_rn(hi[j], lo[j]);
+        float u = 0.f;
+        if (ext > 0.f) u = __fdiv_rn(__fsub_rn(c[j], lo[j]), ext);
+        u = fminf(fmaxf(u, 0.f), 1.f);
+        unsigned v = (unsigned)floorf(__fmul_rn(u, 2097152.0f));
+        k[j] = min(v, 2097151u);
+    }
+    unsigned long long code = 0;
+    for (int b = 20; b >= 0; --b) {
+        code = (code << 1) | ((k[0] >> b) & 1u);
+        code = (code << 1) | ((k[1] >> b) & 1u);
+        code = (code << 1) | ((k[2] >> b) & 1u);
+    }
+    codes[i] = code;
+    keys[i] = code;
+    vals[i] = i;
+}
+
+// --- binary radix tree over buckets (Karras 2012) --------------------------
+__device__ __forceinline__ int bucket_prefix(const unsigned long long* sk, const int* sv, int L, int nb, int i, int j)
+{
+    if (j < 0 || j >= nb) return -1;
+    unsigned long long a = sk[(size_t)i * L], b = sk[(size_t)j * L];
+    if (a != b) return __clzll(a ^ b);
+    return 64 + __clz(sv[(size_t)i * L] ^ sv[(size_t)j * L]);
+}
+
+__global__ void k_karras(const unsigned long long* __restrict__ sk, const int* __restrict__ sv, int L, int nb,
+                         int* __restrict__ left, int* __restrict__ right, int* __restrict__ parent_int,
+                         int* __restrict__ parent_leaf, SdNode* __restrict__ nodes)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nb - 1) return;
+    int d = bucket_prefix(sk, sv, L, nb, i, i + 1) - bucket_prefix(sk, sv, L, nb, i, i - 1) > 0 ? 1 : -1;
+    int dmin = bucket_prefix(sk, sv, L, nb, i, i - d);
+    int lmax = 2;
+    while (bucket_prefix(sk, sv, L, nb, i, i + lmax * d) > dmin) lmax <<= 1;
+    int l = 0;
+    for (int t = lmax >> 1; t >= 1; t >>= 1)
+        if (bucket_prefix(sk, sv, L, nb, i, i + (l + t) * d) > dmin) l += t;
+    int j = i + l * d;
+    int dnode = bucket_prefix(sk, sv, L, nb, i, j);
+    int s = 0;
+    int t = (l + 1) >> 1;
+    for (;;) {
+        if (bucket_prefix(sk, sv, L, nb, i, i + (s + t) * d) > dnode) s += t;
+        if (t == 1) break;
+        t = (t + 1) >> 1;
+    }
+    int gamma = i + s * d + min(d, 0);
+    int lo = min(i, j), hi = max(i, j);
+    int lref = (lo == gamma) ? -(gamma + 1) : gamma;
+    int rref = (hi == gamma + 1) ? -(gamma + 2) : gamma + 1;
+    left[i] = lref;
+    right[i] = rref;
+    if (lref < 0) parent_leaf[gamma] = i; else parent_int[gamma] = i;
+    if (rref < 0) parent_leaf[gamma + 1] = i; else parent_int[gamma + 1] = i;
+    nodes[i].d.x = lref;
+    nodes[i].d.y = rref;
+    if (i == 0) parent_int[0] = -1;
+}
+
+// write child slot `slot` of record `rec`: AABB and far-field mass
+__device__ __forceinline__ void write_slot(SdNode* nodes, int rec, int slot, const float* lo, const float* hi, float nw)
+{
+    float* r = reinterpret_cast<float*>(&nodes[rec]);
+    int o = slot ? 6 : 0;
+    r[o + 0] = lo[0]; r[o + 1] = lo[1]; r[o + 2] = lo[2];
+    r[o + 3] = hi[0]; r[o + 4] = hi[1]; r[o + 5] = hi[2];
+    r[14 + slot] = nw;
+}
+
+// Bottom-up aggregates: a thread per bucket computes the bucket's AABB over
+// all its primitive vertices (exact fp32 min/max), its count and whether it
+// holds only points, then climbs; the second child to arrive at a node
+// merges both children and continues (no thread ever waits).
+__global__ void k_aggregate(Geo g, const int* __restrict__ sorted, int L, int nb, const int* __restrict__ left,
+                            const int* __restrict__ parent_int, const int* __restrict__ parent_leaf,
+                            float* node_box, int* node_count, int* node_pts, float* leaf_box, int* leaf_count,
+                            int* leaf_pts, int* visits, SdNode* nodes, const BuildScalars* bs, float S, int unit)
+{
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    float wfar = 1.f;
+    if (!unit) {
+        float A = (float)max(max(bs->A_E, bs->A_T), 1);
+        wfar = (S == 1.f) ? A : powf(A, S);
+    }
+    float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    int k0 = b * L, k1 = min(k0 + L, g.n);
+    int pts = 1;
+    for (int k = k0; k < k1; ++k) {
+        int p = sorted[k];
+        int nvx = prim_nv(g, p);
+        if (nvx > 1) pts = 0;
+        for (int j = 0; j < nvx; ++j) {
+            float3 v = prim_vertex(g, p, j);
+            lo[0] = fminf(lo[0], v.x); lo[1] = fminf(lo[1], v.y); lo[2] = fminf(lo[2], v.z);
+            hi[0] = fmaxf(hi[0], v.x); hi[1] = fmaxf(hi[1], v.y); hi[2] = fmaxf(hi[2], v.z);
+        }
+    }
+    int count = k1 - k0;
+    for (int j = 0; j < 3; ++j) { leaf_box[6 * b + j] = lo[j]; leaf_box[6 * b + 3 + j] = hi[j]; }
+    leaf_count[b] = count;
+    leaf_pts[b] = pts;
+    float nw = pts ? (float)count : __fmul_rn((float)count, wfar);
+    int par = nb > 1 ? parent_leaf[b] : -1;
+    if (par < 0) { write_slot(nodes, nb - 1, 0, lo, hi, nw); return; }
+    write_slot(nodes, par, left[par] == -(b + 1) ? 0 : 1, lo, hi, nw);
+    int node = par;
+    while (node >= 0) {
+        __threadfence();
+        if (atomicAdd(&visits[node], 1) == 0) return;
+        __threadfence();
+        // both children are final: merge them
+        const SdNode* rn = &nodes[node];
+        int refs[2] = {__ldcg(&rn->d.x), __ldcg(&rn->d.y)};
+        float nlo[3] = {INFINITY, INFINITY, INFINITY}, nhi[3] = {-INFINITY, -INFINITY, -INFINITY};
+        int ncount = 0, npts = 1;
+        for (int c = 0; c < 2; ++c) {
+            const float* bx;
+            int cc, cp;
+            if (refs[c] < 0) {
+                int lb = -refs[c] - 1;
+                bx = leaf_box + 6 * lb;
+                cc = __ldcg(&leaf_count[lb]); cp = __ldcg(&leaf_pts[lb]);
+            } else {
+                bx = node_box + 6 * refs[c];
+                cc = __ldcg(&node_count[refs[c]]); cp = __ldcg(&node_pts[refs[c]]);
+            }
+            for (int j = 0; j < 3; ++j) {
+                nlo[j] = fminf(nlo[j], __ldcg(&bx[j]));
+                nhi[j] = fmaxf(nhi[j], __ldcg(&bx[3 + j]));
+            }
+            ncount += cc;
+            npts &= cp;
+        }
+        for (int j = 0; j < 3; ++j) { node_box[6 * node + j] = nlo[j]; node_box[6 * node + 3 + j] = nhi[j]; }
+        node_count[node] = ncount;
+        node_pts[node] = npts;
+        float nnw = npts ? (float)ncount : __fmul_rn((float)ncount, wfar);
+        int pp = parent_int[node];
+        if (pp < 0) { write_slot(nodes, nb - 1, 0, nlo, nhi, nnw); return; }
+        write_slot(nodes, pp, left[pp] == node ? 0 : 1, nlo, nhi, nnw);
+        node = pp;
+    }
+}
+
+__global__ void k_super_root(SdNode* nodes, int nb)
+{
+    SdNode& r = nodes[nb - 1];
+    r.d.x = nb > 1 ? 0 : -1;
+    r.d.y = SD_NO_CHILD;
+    float* f = reinterpret_cast<float*>(&r);
+    for (int j = 6; j < 12; ++j) f[j] = 0.f;
+    f[15] = 0.f;
+}
+
+// primitives in leaf order
+__global__ void k_gather(Geo g, const int* __restrict__ sorted, const float* __restrict__ params,
+                         float4* __restrict__ hdr, float4* __restrict__ ext)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= g.n) return;
+    int p = sorted[k];
+    float3 a = prim_vertex(g, p, 0);
+    if (p < g.np) {
+        hdr[k] = make_float4(a.x, a.y, a.z, (float)SD_KIND_POINT);
+        return;
+    }
+    if (p < g.np + g.ne) {
+        float3 b = prim_vertex(g, p, 1);
+        hdr[k] = make_float4(a.x, a.y, a.z, (float)SD_KIND_SEG);
+        ext[2 * k] = make_float4(b.x - a.x, b.y - a.y, b.z - a.z, params[2 * p]);
+        ext[2 * k + 1] = make_float4(params[2 * p + 1], 0.f, 0.f, 0.f);
+        return;
+    }
+    float3 b = prim_vertex(g, p, 1), c = prim_vertex(g, p, 2);
+    hdr[k] = make_float4(a.x, a.y, a.z, (float)SD_KIND_TRI);
+    ext[2 * k] = make_float4(b.x - a.x, b.y - a.y, b.z - a.z, params[2 * p]);
+    ext[2 * k + 1] = make_float4(c.x - a.x, c.y - a.y, c.z - a.z, params[2 * p + 1]);
+}
+
+inline int nblk(int64_t n, int t) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + t - 1) / t, 1 << 20)); }
+
+// the library's triangle weight basis as the three float tables of SdParams
+int load_weight_basis(SdParams& P)
+{
+    double b[108];
+    int rc = sd_weight_basis(b);
+    if (rc != SD_OK) return rc;
+    for (int n = 0; n < 36; ++n) {
+        P.tri_base[n] = (float)b[72 + n];          // (v-1)/v column: the barycentre basis
+        P.tri_dv[n] = (float)(b[n] - b[72 + n]);   // 1/v column minus the barycentre column
+        P.tri_de[n] = (float)b[36 + n];            // 1/e column
+    }
+    return SD_OK;
+}
+
+size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace
+
+extern "C" int sd_build(const sd_geometry* g, float alpha, float beta, const sd_build_opts* opts_in,
+                        void* stream, sd_tree** out)
+{
+    if (!out) return SD_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!g) return SD_ERR_INVALID_ARG;
+    sd_build_opts opts;
+    if (opts_in) opts = *opts_in; else sd_default_build_opts(&opts);
+    if (!(alpha > 0.f) || !std::isfinite(alpha) || !(beta >= 0.f) || !std::isfinite(beta)) return SD_ERR_INVALID_ARG;
+    if (opts.leaf_size < 1 || opts.leaf_size > 1024 || !(opts.alpha_u >= 0.f)) return SD_ERR_INVALID_ARG;
+    if (g->pts.n < 0 || g->edges.nv < 0 || g->edges.ne < 0 || g->tris.nv < 0 || g->tris.nf < 0) return SD_ERR_INVALID_ARG;
+    if ((g->pts.n && !g->pts.xyz) || (g->edges.ne && (!g->edges.V || !g->edges.E)) ||
+        (g->tris.nf && (!g->tris.V || !g->tris.F)))
+        return SD_ERR_INVALID_ARG;
+    int64_t n64 = g->pts.n + g->edges.ne + g->tris.nf;
+    const int64_t LIM = (int64_t)1 << 30;
+    if (n64 >= LIM || g->edges.nv >= LIM || g->tris.nv >= LIM || 3 * g->tris.nf >= LIM) return SD_ERR_TOO_LARGE;
+    cudaStream_t st = (cudaStream_t)stream;
+    int dev = 0;
+    cudaGetDevice(&dev);
+
+    Geo geo;
+    geo.P = g->pts.xyz; geo.np = (int)g->pts.n;
+    geo.EV = g->edges.V; geo.nev = g->edges.ne ? (int)g->edges.nv : 0; geo.E = g->edges.E; geo.ne = (int)g->edges.ne;
+    geo.TV = g->tris.V; geo.ntv = g->tris.nf ? (int)g->tris.nv : 0; geo.F = g->tris.F; geo.nf = (int)g->tris.nf;
+    geo.n = (int)n64;
+    const int n = geo.n;
+    const int L = opts.leaf_size;
+    const int nb = n > 0 ? (n + L - 1) / L : 0;
+    const int ni = nb > 0 ? nb - 1 : 0;
+    int kinds = (geo.np ? SD_HAS_PTS : 0) | (geo.ne ? SD_HAS_SEGS : 0) | (geo.nf ? SD_HAS_TRIS : 0);
+
+    sd_tree* t = new sd_tree();
+    std::memset(t, 0, sizeof(*t));
+    t->device = dev;
+    t->kinds = kinds;
+    t->weights_unit = opts.weights == SD_WEIGHTS_UNIT;
+    t->paper_metric = opts.paper_metric != 0;
+    float S = alpha / std::max(alpha, opts.alpha_u);
+
+    // persistent memory
+    size_t off = 0;
+    auto carve = [&](size_t bytes) { size_t o = off; off += align_up(std::max<size_t>(bytes, 1)); return o; };
+    size_t o_nodes = carve(sizeof(SdNode) * std::max(nb, 1));
+    size_t o_hdr = carve(sizeof(float4) * std::max(n, 1));
+    size_t o_ext = carve((kinds & (SD_HAS_SEGS | SD_HAS_TRIS)) ? sizeof(float4) * 2 * (size_t)n : 16);
+    size_t o_codes = carve(sizeof(uint64_t) * std::max(n, 1));
+    size_t o_sorted = carve(sizeof(int) * std::max(n, 1));
+    size_t o_left = carve(sizeof(int) * std::max(ni, 1));
+    size_t o_right = carve(sizeof(int) * std::max(ni, 1));
+    size_t o_nbox = carve(sizeof(float) * 6 * std::max(ni, 1));
+    size_t o_ncnt = carve(sizeof(int) * std::max(ni, 1));
+    size_t o_lbox = carve(sizeof(float) * 6 * std::max(nb, 1));
+    size_t o_lcnt = carve(sizeof(int) * std::max(nb, 1));
+    size_t o_params = carve(sizeof(float) * 2 * std::max(n, 1));
+    size_t o_status = carve(sizeof(int) * 4);
+    t->mem_bytes = off;
+    cudaError_t ce = cudaMalloc(&t->mem, off);
+    if (ce != cudaSuccess) { delete t; cudaGetLastError(); return SD_ERR_OOM; }
+    char* base = (char*)t->mem;
+    t->nodes = (SdNode*)(base + o_nodes);
+    t->hdr = (float4*)(base + o_hdr);
+    t->ext = (float4*)(base + o_ext);
+    t->codes = (uint64_t*)(base + o_codes);
+    t->sorted = (int32_t*)(base + o_sorted);
+    t->left = (int32_t*)(base + o_left);
+    t->right = (int32_t*)(base + o_right);
+    t->node_box = (float*)(base + o_nbox);
+    t->node_count = (int32_t*)(base + o_ncnt);
+    t->leaf_box = (float*)(base + o_lbox);
+    t->leaf_count = (int32_t*)(base + o_lcnt);
+    t->params = (float*)(base + o_params);
+    t->status = (int*)(base + o_status);
+
+    // temporary memory
+    size_t toff = 0;
+    auto tcarve = [&](size_t bytes) { size_t o = toff; toff += align_up(std::max<size_t>(bytes, 1)); return o; };
+    unsigned hcap = 1;
+    while (hcap < (unsigned)std::max(2 * 3 * geo.nf, 2)) hcap <<= 1;
+    size_t t_bs = tcarve(sizeof(BuildScalars));
+    size_t t_k1 = tcarve(sizeof(unsigned long long) * std::max(n, 1));
+    size_t t_v0 = tcarve(sizeof(int) * std::max(n, 1));
+    size_t t_v1 = tcarve(sizeof(int) * std::max(n, 1));
+    size_t t_k0 = tcarve(sizeof(unsigned long long) * std::max(n, 1));
+    size_t t_hist = tcarve(sizeof(uint32_t) * sdsort::hist_words(std::max(n, 1)));
+    size_t t_ecnt = tcarve(sizeof(int) * std::max(geo.nev, 1));
+    size_t t_vcnt = tcarve(sizeof(int) * std::max(geo.ntv, 1));
+    size_t t_hkeys = tcarve(geo.nf ? sizeof(unsigned long long) * hcap : 8);
+    size_t t_hcnt = tcarve(geo.nf ? sizeof(int) * hcap : 4);
+    size_t t_pint = tcarve(sizeof(int) * std::max(nb, 1));
+    size_t t_pleaf = tcarve(sizeof(int) * std::max(nb, 1));
+    size_t t_visits = tcarve(sizeof(int) * std::max(nb, 1));
+    size_t t_npts = tcarve(sizeof(int) * std::max(nb, 1));
+    size_t t_lpts = tcarve(sizeof(int) * std::max(nb, 1));
+    void* tmp = nullptr;
+    ce = cudaMallocAsync(&tmp, toff, st);
+    if (ce != cudaSuccess) { cudaFree(t->mem); delete t; cudaGetLastError(); return SD_ERR_OOM; }
+    char* tb = (char*)tmp;
+    BuildScalars* bs = (BuildScalars*)(tb + t_bs);
+    auto* k0 = (unsigned long long*)(tb + t_k0);
+    auto* k1 = (unsigned long long*)(tb + t_k1);
+    int* v0 = (int*)(tb + t_v0);
+    int* v1 = (int*)(tb + t_v1);
+    uint32_t* hist = (uint32_t*)(tb + t_hist);
+    int* ecnt = (int*)(tb + t_ecnt);
+    int* vcnt = (int*)(tb + t_vcnt);
+    auto* hkeys = (unsigned long long*)(tb + t_hkeys);
+    int* hcnt = (int*)(tb + t_hcnt);
+    int* pint = (int*)(tb + t_pint);
+    int* pleaf = (int*)(tb + t_pleaf);
+    int* visits = (int*)(tb + t_visits);
+    int* npts = (int*)(tb + t_npts);
+    int* lpts = (int*)(tb + t_lpts);
+
+    BuildScalars init;
+    std::memset(&init, 0, sizeof(init));
+    for (int j = 0; j < 3; ++j) { init.box[j] = 0xffffffffu; init.box[3 + j] = 0u; }
+    init.A_E = 1; init.A_T = 1;
+    cudaMemcpyAsync(bs, &init, sizeof(init), cudaMemcpyHostToDevice, st);
+    cudaMemsetAsync(t->status, 0, sizeof(int) * 4, st);
+    cudaMemsetAsync(t->params, 0, sizeof(float) * 2 * std::max(n, 1), st);
+    cudaMemsetAsync(t->nodes, 0, sizeof(SdNode) * std::max(nb, 1), st);
+    cudaMemsetAsync(visits, 0, sizeof(int) * std::max(nb, 1), st);
+
+    const int T = 256;
+    int nl = 0;   // kernel launches of this build
+    // validation + scene box over every vertex
+    if (geo.np) { ++nl; k_vertices<<<std::min(nblk(geo.np, T), 1024), T, 0, st>>>(geo.P, geo.np, bs); }
+    if (geo.nev) { ++nl; k_vertices<<<std::min(nblk(geo.nev, T), 1024), T, 0, st>>>(geo.EV, geo.nev, bs); }
+    if (geo.ntv) { ++nl; k_vertices<<<std::min(nblk(geo.ntv, T), 1024), T, 0, st>>>(geo.TV, geo.ntv, bs); }
+    if (geo.ne) { ++nl; k_check_index<<<std::min(nblk(2 * (int64_t)geo.ne, T), 1024), T, 0, st>>>(geo.E, 2 * (int64_t)geo.ne, geo.nev, bs); }
+    if (geo.nf) { ++nl; k_check_index<<<std::min(nblk(3 * (int64_t)geo.nf, T), 1024), T, 0, st>>>(geo.F, 3 * (int64_t)geo.nf, geo.ntv, bs); }
+    // the index checks must pass before any kernel dereferences an index
+    BuildScalars hb;
+    cudaMemcpyAsync(&hb, bs, sizeof(hb), cudaMemcpyDeviceToHost, st);
+    ce = cudaStreamSynchronize(st);
+    int status = SD_OK;
+    if (ce != cudaSuccess) status = sd_cuda_status(ce);
+    else if (hb.status & ST_INDEX) status = SD_ERR_INDEX;
+    else if (hb.status & ST_NONFINITE) status = SD_ERR_NONFINITE;
+    if (status != SD_OK) {
+        sd_count_launches(nl);
+        cudaFreeAsync(tmp, st);
+        cudaStreamSynchronize(st);
+        cudaFree(t->mem);
+        delete t;
+        return status;
+    }
+
+    // incidence counts and weight parameters
+    if (geo.ne) {
+        cudaMemsetAsync(ecnt, 0, sizeof(int) * geo.nev, st);
+        ++nl;
+        k_count_slots<<<std::min(nblk(2 * (int64_t)geo.ne, T), 4096), T, 0, st>>>(geo.E, 2 * (int64_t)geo.ne, ecnt);
+        ++nl;
+        k_edge_params<<<nblk(geo.ne, T), T, 0, st>>>(geo.E, geo.ne, ecnt, t->params, geo.np, bs);
+    }
+    if (geo.nf) {
+        cudaMemsetAsync(vcnt, 0, sizeof(int) * geo.ntv, st);
+        cudaMemsetAsync(hkeys, 0xff, sizeof(unsigned long long) * hcap, st);
+        cudaMemsetAsync(hcnt, 0, sizeof(int) * hcap, st);
+        ++nl;
+        k_count_slots<<<std::min(nblk(3 * (int64_t)geo.nf, T), 4096), T, 0, st>>>(geo.F, 3 * (int64_t)geo.nf, vcnt);
+        ++nl;
+        k_edge_insert<<<nblk(3 * (int64_t)geo.nf, T), T, 0, st>>>(geo.F, geo.nf, hkeys, hcnt, hcap - 1);
+        ++nl;
+        k_tri_params<<<nblk(geo.nf, T), T, 0, st>>>(geo.F, geo.nf, vcnt, hkeys, hcnt, hcap - 1, t->params,
+                                                     geo.np + geo.ne, bs);
+    }
+    if (n > 0) {
+        // Morton order
+        ++nl;
+        k_morton<<<nblk(n, T), T, 0, st>>>(geo, bs, (unsigned long long*)t->codes, k0, v0);
+        int where = sdsort::sort_pairs<unsigned long long, int>(k0, v0, k1, v1, n, 64, hist, st, &nl);
+        unsigned long long* sk = where ? k1 : k0;
+        int* sv = where ? v1 : v0;
+        cudaMemcpyAsync(t->sorted, sv, sizeof(int) * n, cudaMemcpyDeviceToDevice, st);
+        // topology
+        if (nb > 1) {
+            ++nl;
+            k_karras<<<nblk(nb - 1, T), T, 0, st>>>(sk, sv, L, nb, t->left, t->right, pint, pleaf, t->nodes);
+        }
+        ++nl;
+        k_super_root<<<1, 1, 0, st>>>(t->nodes, nb);
+        // aggregates
+        ++nl;
+        k_aggregate<<<nblk(nb, T), T, 0, st>>>(geo, sv, L, nb, t->left, pint, pleaf, t->node_box, t->node_count,
+                                                npts, t->leaf_box, t->leaf_count, lpts, visits, t->nodes, bs, S,
+                                                t->weights_unit);
+        ++nl;
+        k_gather<<<nblk(n, T), T, 0, st>>>(geo, sv, t->params, t->hdr, t->ext);
+    }
+    cudaMemcpyAsync(&hb, bs, sizeof(hb), cudaMemcpyDeviceToHost, st);
+    cudaFreeAsync(tmp, st);
+    sd_count_launches(nl);
+    ce = cudaStreamSynchronize(st);
+    if (ce == cudaSuccess) ce = cudaGetLastError();
+    if (ce != cudaSuccess) {
+        cudaFree(t->mem);
+        delete t;
+        return sd_cuda_status(ce);
+    }
+
+    sd_tree_info& inf = t->info;
+    inf.n_prims = n; inf.n_points = geo.np; inf.n_edges = geo.ne; inf.n_tris = geo.nf;
+    inf.n_buckets = nb; inf.leaf_size = L;
+    inf.alpha = alpha; inf.beta = beta; inf.alpha_u = opts.alpha_u; inf.S = S;
+    inf.A_E = t->weights_unit ? 1.f : (float)hb.A_E;
+    inf.A_T = t->weights_unit ? 1.f : (float)hb.A_T;
+    float A = std::max(inf.A_E, inf.A_T);
+    inf.w_far = t->weights_unit ? 1.f : (S == 1.f ? A : std::pow(A, S));
+    for (int j = 0; j < 3; ++j) {
+        inf.scene_lo[j] = n ? key2f(hb.box[j]) : 0.f;
+        inf.scene_hi[j] = n ? key2f(hb.box[3 + j]) : 0.f;
+    }
+    inf.device_bytes = (int64_t)t->mem_bytes;
+
+    SdParams& P = t->P;
+    int wrc = load_weight_basis(P);
+    if (wrc != SD_OK) { cudaFree(t->mem); delete t; return wrc; }
+    P.nodes = t->nodes;
+    P.hdr = t->hdr;
+    P.ext = t->ext;
+    P.root_record = nb - 1;
+    P.n_prims = n;
+    P.L = L;
+    P.beta2 = beta * beta;
+    const float LOG2E = 1.4426950408889634f;
+    P.alpha2 = alpha * LOG2E;
+    P.inv_alpha2 = 1.f / P.alpha2;
+    P.S = S;
+    P.A_E = inf.A_E;
+    P.A_T = inf.A_T;
+    P.kw = t->paper_metric ? S / (alpha * alpha) : S / alpha;
+    P.unit_weights = t->weights_unit;
+    P.s_is_one = S == 1.f;
+    *out = t;
+    return SD_OK;
+}
+
+extern "C" int sd_tree_get_info(const sd_tree* t, sd_tree_info* info)
+{
+    if (!t || !info) return SD_ERR_INVALID_ARG;
+    *info = t->info;
+    return SD_OK;
+}
+
+extern "C" int sd_tree_export(const sd_tree* t, sd_tree_view* v)
+{
+    if (!t || !v) return SD_ERR_INVALID_ARG;
+    int64_t n = t->info.n_prims, nb = t->info.n_buckets, ni = nb > 0 ? nb - 1 : 0;
+    cudaError_t e = cudaSuccess;
+    auto cp = [&](void* dst, const void* src, size_t bytes) {
+        if (dst && bytes && e == cudaSuccess) e = cudaMemcpy(dst, src, bytes, cudaMemcpyDeviceToHost);
+    };
+    cp(v->codes, t->codes, sizeof(uint64_t) * n);
+    cp(v->sorted, t->sorted, sizeof(int32_t) * n);
+    cp(v->left, t->left, sizeof(int32_t) * ni);
+    cp(v->right, t->right, sizeof(int32_t) * ni);
+    cp(v->node_count, t->node_count, sizeof(int32_t) * ni);
+    cp(v->leaf_count, t->leaf_count, sizeof(int32_t) * nb);
+    cp(v->params, t->params, sizeof(float) * 2 * n);
+    if (e == cudaSuccess && (v->node_lo || v->node_hi) && ni) {
+        std::vector<float> box(6 * ni);
+        cp(box.data(), t->node_box, sizeof(float) * 6 * ni);
+        for (int64_t i = 0; i < ni; ++i)
+            for (int j = 0; j < 3; ++j) {
+                if (v->node_lo) v->node_lo[3 * i + j] = box[6 * i + j];
+                if (v->node_hi) v->node_hi[3 * i + j] = box[6 * i + 3 + j];
+            }
+    }
+    if (e == cudaSuccess && (v->leaf_lo || v->leaf_hi) && nb) {
+        std::vector<float> box(6 * nb);
+        cp(box.data(), t->leaf_box, sizeof(float) * 6 * nb);
+        for (int64_t i = 0; i < nb; ++i)
+            for (int j = 0; j < 3; ++j) {
+                if (v->leaf_lo) v->leaf_lo[3 * i + j] = box[6 * i + j];
+                if (v->leaf_hi) v->leaf_hi[3 * i + j] = box[6 * i + 3 + j];
+            }
+    }
+    return e == cudaSuccess ? SD_OK : sd_cuda_status(e);
+}
+
+extern "C" void sd_free(sd_tree* t)
+{
+    if (!t) return;
+    if (t->mem) cudaFree(t->mem);
+    delete t;
+}
