@@ -725,7 +725,8 @@ static void acc_push(acc_t *a, term_t t)
 
 /* The Barnes-Hut condition |B| / d(y_B, q) < beta with y_B the closest point
    of the box (Sec. 3.5, App. D). Decision mode 0 takes it in FP32 as
-   diag^2 < beta^2 * dbox^2 with the operation order fixed below; mode 1 in
+   diag^2 < beta^2 * dbox^2 with the operation order fixed below (squares
+   summed as fma(z, z, fma(y, y, x * x)), each fma rounded once); mode 1 in
    FP64 as the ratio. A query inside the box (d = 0) always opens it. */
 static int bh_condition(const bh_ctx *c, const float *lo, const float *hi, const double *q, double *margin)
 {
@@ -738,10 +739,10 @@ static int bh_condition(const bh_ctx *c, const float *lo, const float *hi, const
             dx[j] = m > 0.0f ? m : 0.0f;
             ex[j] = hi[j] - lo[j];
         }
-        float x0 = dx[0] * dx[0], x1 = dx[1] * dx[1], x2 = dx[2] * dx[2];
-        float dbox2 = (x0 + x1) + x2;
-        float y0 = ex[0] * ex[0], y1 = ex[1] * ex[1], y2 = ex[2] * ex[2];
-        float diag2 = (y0 + y1) + y2;
+        float x0 = dx[0] * dx[0];
+        float dbox2 = fmaf(dx[2], dx[2], fmaf(dx[1], dx[1], x0));
+        float y0 = ex[0] * ex[0];
+        float diag2 = fmaf(ex[2], ex[2], fmaf(ex[1], ex[1], y0));
         float rhs = c->beta2f * dbox2;
         if (margin && dbox2 > 0.0f) {
             double r = sqrt((double)diag2) / sqrt((double)dbox2);

@@ -262,14 +262,21 @@ __global__ void k_karras(const unsigned long long* __restrict__ sk, const int* _
     if (i == 0) parent_int[0] = -1;
 }
 
-// write child slot `slot` of record `rec`: AABB and far-field mass
-__device__ __forceinline__ void write_slot(SdNode* nodes, int rec, int slot, const float* lo, const float* hi, float nw)
+// write child slot `slot` of record `rec` (interleaved AABB with negated upper
+// corner, squared diagonal) and the child's far-field mass
+__device__ __forceinline__ void write_slot(SdNode* nodes, float2* nw2, int rec, int slot, const float* lo,
+                                           const float* hi, float nw)
 {
     float* r = reinterpret_cast<float*>(&nodes[rec]);
-    int o = slot ? 6 : 0;
-    r[o + 0] = lo[0]; r[o + 1] = lo[1]; r[o + 2] = lo[2];
-    r[o + 3] = hi[0]; r[o + 4] = hi[1]; r[o + 5] = hi[2];
-    r[14 + slot] = nw;
+    r[0 + slot] = lo[0];
+    r[2 + slot] = lo[1];
+    r[4 + slot] = lo[2];
+    r[6 + slot] = -hi[0];
+    r[8 + slot] = -hi[1];
+    r[10 + slot] = -hi[2];
+    r[14 + slot] = box_diag2(lo, hi);
+    float* w = reinterpret_cast<float*>(&nw2[rec]);
+    w[slot] = nw;
 }
 
 // Bottom-up aggregates: a thread per bucket computes the bucket's AABB over
@@ -279,7 +286,8 @@ __device__ __forceinline__ void write_slot(SdNode* nodes, int rec, int slot, con
 __global__ void k_aggregate(Geo g, const int* __restrict__ sorted, int L, int nb, const int* __restrict__ left,
                             const int* __restrict__ parent_int, const int* __restrict__ parent_leaf,
                             float* node_box, int* node_count, int* node_pts, float* leaf_box, int* leaf_count,
-                            int* leaf_pts, int* visits, SdNode* nodes, const BuildScalars* bs, float S, int unit)
+                            int* leaf_pts, int* visits, SdNode* nodes, float2* nw2, const BuildScalars* bs, float S,
+                            int unit)
 {
     int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= nb) return;
@@ -307,8 +315,8 @@ __global__ void k_aggregate(Geo g, const int* __restrict__ sorted, int L, int nb
     leaf_pts[b] = pts;
     float nw = pts ? (float)count : __fmul_rn((float)count, wfar);
     int par = nb > 1 ? parent_leaf[b] : -1;
-    if (par < 0) { write_slot(nodes, nb - 1, 0, lo, hi, nw); return; }
-    write_slot(nodes, par, left[par] == -(b + 1) ? 0 : 1, lo, hi, nw);
+    if (par < 0) { write_slot(nodes, nw2, nb - 1, 0, lo, hi, nw); return; }
+    write_slot(nodes, nw2, par, left[par] == -(b + 1) ? 0 : 1, lo, hi, nw);
     int node = par;
     while (node >= 0) {
         __threadfence();
@@ -342,20 +350,21 @@ __global__ void k_aggregate(Geo g, const int* __restrict__ sorted, int L, int nb
         node_pts[node] = npts;
         float nnw = npts ? (float)ncount : __fmul_rn((float)ncount, wfar);
         int pp = parent_int[node];
-        if (pp < 0) { write_slot(nodes, nb - 1, 0, nlo, nhi, nnw); return; }
-        write_slot(nodes, pp, left[pp] == node ? 0 : 1, nlo, nhi, nnw);
+        if (pp < 0) { write_slot(nodes, nw2, nb - 1, 0, nlo, nhi, nnw); return; }
+        write_slot(nodes, nw2, pp, left[pp] == node ? 0 : 1, nlo, nhi, nnw);
         node = pp;
     }
 }
 
-__global__ void k_super_root(SdNode* nodes, int nb)
+__global__ void k_super_root(SdNode* nodes, float2* nw2, int nb)
 {
     SdNode& r = nodes[nb - 1];
     r.d.x = nb > 1 ? 0 : -1;
     r.d.y = SD_NO_CHILD;
     float* f = reinterpret_cast<float*>(&r);
-    for (int j = 6; j < 12; ++j) f[j] = 0.f;
+    for (int j = 1; j < 12; j += 2) f[j] = 0.f;   // slot 1 is empty
     f[15] = 0.f;
+    nw2[nb - 1].y = 0.f;
 }
 
 // primitives in leaf order
@@ -447,6 +456,7 @@ extern "C" int sd_build(const sd_geometry* g, float alpha, float beta, const sd_
     size_t off = 0;
     auto carve = [&](size_t bytes) { size_t o = off; off += align_up(std::max<size_t>(bytes, 1)); return o; };
     size_t o_nodes = carve(sizeof(SdNode) * std::max(nb, 1));
+    size_t o_nw = carve(sizeof(float2) * std::max(nb, 1));
     size_t o_hdr = carve(sizeof(float4) * std::max(n, 1));
     size_t o_ext = carve((kinds & (SD_HAS_SEGS | SD_HAS_TRIS)) ? sizeof(float4) * 2 * (size_t)n : 16);
     size_t o_codes = carve(sizeof(uint64_t) * std::max(n, 1));
@@ -464,6 +474,7 @@ extern "C" int sd_build(const sd_geometry* g, float alpha, float beta, const sd_
     if (ce != cudaSuccess) { delete t; cudaGetLastError(); return SD_ERR_OOM; }
     char* base = (char*)t->mem;
     t->nodes = (SdNode*)(base + o_nodes);
+    t->nw2 = (float2*)(base + o_nw);
     t->hdr = (float4*)(base + o_hdr);
     t->ext = (float4*)(base + o_ext);
     t->codes = (uint64_t*)(base + o_codes);
@@ -586,12 +597,12 @@ extern "C" int sd_build(const sd_geometry* g, float alpha, float beta, const sd_
             k_karras<<<nblk(nb - 1, T), T, 0, st>>>(sk, sv, L, nb, t->left, t->right, pint, pleaf, t->nodes);
         }
         ++nl;
-        k_super_root<<<1, 1, 0, st>>>(t->nodes, nb);
+        k_super_root<<<1, 1, 0, st>>>(t->nodes, t->nw2, nb);
         // aggregates
         ++nl;
         k_aggregate<<<nblk(nb, T), T, 0, st>>>(geo, sv, L, nb, t->left, pint, pleaf, t->node_box, t->node_count,
-                                                npts, t->leaf_box, t->leaf_count, lpts, visits, t->nodes, bs, S,
-                                                t->weights_unit);
+                                                npts, t->leaf_box, t->leaf_count, lpts, visits, t->nodes, t->nw2,
+                                                bs, S, t->weights_unit);
         ++nl;
         k_gather<<<nblk(n, T), T, 0, st>>>(geo, sv, t->params, t->hdr, t->ext);
     }
@@ -624,6 +635,7 @@ extern "C" int sd_build(const sd_geometry* g, float alpha, float beta, const sd_
     int wrc = load_weight_basis(P);
     if (wrc != SD_OK) { cudaFree(t->mem); delete t; return wrc; }
     P.nodes = t->nodes;
+    P.nw2 = t->nw2;
     P.hdr = t->hdr;
     P.ext = t->ext;
     P.root_record = nb - 1;

@@ -12,14 +12,16 @@
 // ---------------------------------------------------------------------------
 // One record per internal node of the binary radix tree (Karras numbering,
 // 0 .. nb-2) plus a super-root record at index nb-1 whose child 0 is the
-// root. Each record holds the data Alg. 1 needs to decide on BOTH children
-// (App. D): their AABBs, child references and far-field masses n_B * w_B,
-// so one 64-byte fetch tests two nodes.
-//   a = (c0.lo.x, c0.lo.y, c0.lo.z, c0.hi.x)
-//   b = (c0.hi.y, c0.hi.z, c1.lo.x, c1.lo.y)
-//   c = (c1.lo.z, c1.hi.x, c1.hi.y, c1.hi.z)
-//   d = (ref0, ref1, bits(nw0), bits(nw1))
+// root. Each record holds what the Barnes-Hut test of Alg. 1 / App. D needs
+// for BOTH children, interleaved so that the two tests run as packed
+// two-wide fp32 operations: lower corners, negated upper corners (so that
+// q - hi is an exact packed add), child references and squared diagonals.
+//   a = (c0.lo.x, c1.lo.x, c0.lo.y, c1.lo.y)
+//   b = (c0.lo.z, c1.lo.z, -c0.hi.x, -c1.hi.x)
+//   c = (-c0.hi.y, -c1.hi.y, -c0.hi.z, -c1.hi.z)
+//   d = (ref0, ref1, bits(diag2_0), bits(diag2_1))
 // ref >= 0: internal node; ref < 0: leaf bucket -(ref + 1); SD_NO_CHILD: none.
+// The far-field masses n_B w_B of both children sit in nw2[record].
 struct __align__(16) SdNode {
     float4 a, b, c;
     int4 d;
@@ -37,9 +39,10 @@ enum { SD_HAS_PTS = 1, SD_HAS_SEGS = 2, SD_HAS_TRIS = 4 };
 // Parameters a traversal needs, passed by value to the kernels.
 struct SdParams {
     const SdNode* nodes;
+    const float2* nw2;    // far-field masses of both children, per record
     const float4* hdr;
     const float4* ext;
-    int root_record;      // nb - 1
+    int root_record;      // nb - 1 (also the offset of bucket ids in nw)
     int n_prims;
     int L;
     float beta2;          // beta*beta rounded to fp32 (the Barnes-Hut test is taken in fp32)
@@ -69,6 +72,7 @@ struct sd_tree {
     void* mem;
     size_t mem_bytes;
     SdNode* nodes;        // nb records (nb - 1 internal + super-root)
+    float2* nw2;          // nb pairs of far-field masses
     float4* hdr;          // n
     float4* ext;          // 2n (only when edges or triangles exist)
     uint64_t* codes;      // n, original order
@@ -149,11 +153,25 @@ __device__ __forceinline__ void lse_add(Lse& L, float y, float w, float3 v)
     L.m = up ? y : L.m;
 }
 
+// fp32 sum of squares in the fixed order fma(z, z, fma(y, y, x * x)), each
+// step rounded once (never re-associated or split by the compiler)
+__device__ __forceinline__ float sumsq3(float x, float y, float z)
+{
+    return __fmaf_rn(z, z, __fmaf_rn(y, y, __fmul_rn(x, x)));
+}
+
+// squared diagonal |B|^2 of an AABB (App. D), stored in the tree records
+__device__ __forceinline__ float box_diag2(const float* lo, const float* hi)
+{
+    return sumsq3(__fsub_rn(hi[0], lo[0]), __fsub_rn(hi[1], lo[1]), __fsub_rn(hi[2], lo[2]));
+}
+
 // The Barnes-Hut test |B|^2 < beta^2 d(y_B, q)^2 (App. D) in fp32 with a fixed
-// operation order and no contraction, so that its outcome is reproducible
-// bit for bit. Returns dbox2 and the (signed) offset q - y_B.
+// operation order, so that its outcome is reproducible bit for bit. Returns
+// dbox2 and the signed offset q - y_B (y_B = closest point of the box).
+// (Scalar form, used by the brute-force-free paths and the build checks.)
 __device__ __forceinline__ bool bh_far(float3 q, float lx, float ly, float lz, float hx, float hy, float hz,
-                                       float beta2, float& dbox2, float3& off)
+                                       float diag2, float beta2, float& dbox2, float3& off)
 {
     float ax = __fsub_rn(lx, q.x), bx = __fsub_rn(q.x, hx);
     float ay = __fsub_rn(ly, q.y), by = __fsub_rn(q.y, hy);
@@ -161,11 +179,48 @@ __device__ __forceinline__ bool bh_far(float3 q, float lx, float ly, float lz, f
     float dx = fmaxf(fmaxf(ax, bx), 0.f);
     float dy = fmaxf(fmaxf(ay, by), 0.f);
     float dz = fmaxf(fmaxf(az, bz), 0.f);
-    dbox2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
-    float ex = __fsub_rn(hx, lx), ey = __fsub_rn(hy, ly), ez = __fsub_rn(hz, lz);
-    float diag2 = __fadd_rn(__fadd_rn(__fmul_rn(ex, ex), __fmul_rn(ey, ey)), __fmul_rn(ez, ez));
-    off = f3(fmaxf(bx, 0.f) - fmaxf(ax, 0.f), fmaxf(by, 0.f) - fmaxf(ay, 0.f), fmaxf(bz, 0.f) - fmaxf(az, 0.f));
+    dbox2 = sumsq3(dx, dy, dz);
+    // q > hi: offset +d (b > 0); q < lo: offset -d (b < 0); inside: 0
+    off = f3(copysignf(dx, bx), copysignf(dy, by), copysignf(dz, bz));
     return diag2 < __fmul_rn(beta2, dbox2);
+}
+
+// Add two terms w0 2^y0 and w1 2^y1 without branches. A term that is absent
+// has w = 0 and y = SD_NEG (finite, so that differences never give NaN); the
+// running max m starts at SD_NEG as well.
+#define SD_NEG (-8.5e37f)
+template <bool GRAD>
+__device__ __forceinline__ void lse_add2(Lse& L, float y0, float w0, float3 v0, float y1, float w1, float3 v1)
+{
+    float mn = fmaxf(L.m, fmaxf(y0, y1));
+    float eo = sd_ex2(L.m - mn);
+    float c0 = w0 * sd_ex2(y0 - mn);
+    float c1 = w1 * sd_ex2(y1 - mn);
+    L.s = fmaf(L.s, eo, c0 + c1);
+    if (GRAD) {
+        L.gx = fmaf(L.gx, eo, fmaf(c0, v0.x, c1 * v1.x));
+        L.gy = fmaf(L.gy, eo, fmaf(c0, v0.y, c1 * v1.y));
+        L.gz = fmaf(L.gz, eo, fmaf(c0, v0.z, c1 * v1.z));
+    }
+    L.m = mn;
+}
+
+// merge a second LSE state (m2, s2, g2) into L
+template <bool GRAD>
+__device__ __forceinline__ void lse_merge(Lse& L, float m2, float s2, float gx2, float gy2, float gz2)
+{
+    float dl = m2 - L.m;
+    float e = sd_ex2(-fabsf(dl));
+    bool up = dl > 0.f;
+    float a = up ? e : 1.f;
+    float b = up ? 1.f : e;
+    L.s = fmaf(L.s, a, s2 * b);
+    if (GRAD) {
+        L.gx = fmaf(L.gx, a, gx2 * b);
+        L.gy = fmaf(L.gy, a, gy2 * b);
+        L.gz = fmaf(L.gz, a, gz2 * b);
+    }
+    L.m = up ? m2 : L.m;
 }
 
 // ---------------------------------------------------------------------------

@@ -22,118 +22,260 @@ namespace {
 // consecutive queries of the Morton order and walk the tree together on one
 // warp-uniform stack of (record, lane mask) entries in shared memory. Every
 // lane takes its own Barnes-Hut decisions (so each query gets exactly the
-// terms of Alg. 1); a record is fetched once per warp and broadcast, a child
-// is pushed if any lane needs it opened, and a leaf is evaluated by the lanes
-// that reach it.
+// terms of Alg. 1); a record is fetched once per warp and broadcast, and a
+// child is pushed if any lane needs it opened. Exact leaf terms are not
+// evaluated where they are found: each (query lane, primitive) pair goes to
+// a per-warp queue, and every 32 queued pairs are evaluated by the 32 lanes
+// at once, then folded into their owners' LogSumExp states by warp shuffles.
+// Warps are persistent and take packets from a global counter.
 constexpr int PK_STACK = 128;     // > depth + 1 of any radix tree over 95-bit keys
+constexpr int PK_QCAP = 64;       // leaf queue: < 32 pending + at most 32 pushed at once
 constexpr int PK_MAX_THREADS = 256;
+constexpr int PK_WARP_INTS = 2 * PK_STACK + 2 * PK_QCAP + 32;   // per-warp shared memory, in ints
 
+struct WarpShared {
+    int2* stack;
+    int2* queue;
+    int* lead;      // lead[owner lane] = lane holding the owner's merged partial sum, or -1
+};
+
+// Evaluate n <= 32 queued (owner lane, primitive) pairs, one per lane, and
+// fold each result into its owner's accumulator.
 template <int KINDS, bool GRAD>
-__device__ __forceinline__ void packet_child(const SdParams& P, float3 q, bool mine, float lx, float ly, float lz,
-                                             float hx, float hy, float hz, int ref, float nw, Lse& acc,
-                                             int2* st, int& sp, int lane, int& ntest, int& nfar, int& nleaf,
-                                             bool& overflow)
+__device__ __forceinline__ void flush_queue(const SdParams& P, float3 q, const int2* items, int n, const WarpShared& ws,
+                                            int lane, Lse& acc)
 {
-    bool need = false, leaf = false;
-    if (mine) {
-        ++ntest;
-        float dbox2;
-        float3 off;
-        if (bh_far(q, lx, ly, lz, hx, hy, hz, P.beta2, dbox2, off)) {
-            // far field of App. D at the box's closest point y_B
-            float rs = rsqrtf(dbox2);
-            lse_add<GRAD>(acc, -P.alpha2 * (dbox2 * rs), nw, scale(off, rs));
-            ++nfar;
-        } else if (ref < 0) {
-            leaf = true;
-        } else {
-            need = true;
+    __syncwarp();
+    bool has = lane < n;
+    int2 it = has ? items[lane] : make_int2(lane, 0);
+    int owner = it.x;
+    float3 qo = f3(__shfl_sync(0xffffffffu, q.x, owner), __shfl_sync(0xffffffffu, q.y, owner),
+                   __shfl_sync(0xffffffffu, q.z, owner));
+    float tm = -INFINITY, ts = 0.f, tx = 0.f, ty = 0.f, tz = 0.f;
+    if (has) {
+        float y, w;
+        float3 v;
+        leaf_term<KINDS, GRAD>(P, qo, it.y, y, w, v);
+        tm = y; ts = w;
+        if (GRAD) { tx = w * v.x; ty = w * v.y; tz = w * v.z; }
+    }
+    // combine the terms of each owner in its group leader
+    unsigned key = has ? (unsigned)owner : 32u + (unsigned)lane;
+    unsigned peers = __match_any_sync(0xffffffffu, key);
+    int leader = __ffs(peers) - 1;
+    unsigned rest = (lane == leader) ? (peers & (peers - 1u)) : 0u;
+    while (__any_sync(0xffffffffu, rest != 0u)) {
+        int src = rest ? __ffs(rest) - 1 : lane;
+        float m2 = __shfl_sync(0xffffffffu, tm, src), s2 = __shfl_sync(0xffffffffu, ts, src);
+        float x2 = 0.f, y2 = 0.f, z2 = 0.f;
+        if (GRAD) {
+            x2 = __shfl_sync(0xffffffffu, tx, src);
+            y2 = __shfl_sync(0xffffffffu, ty, src);
+            z2 = __shfl_sync(0xffffffffu, tz, src);
+        }
+        if (rest) {
+            Lse t{tm, ts, tx, ty, tz};
+            lse_merge<GRAD>(t, m2, s2, x2, y2, z2);
+            tm = t.m; ts = t.s; tx = t.gx; ty = t.gy; tz = t.gz;
+            rest &= rest - 1u;
         }
     }
-    if (__ballot_sync(0xffffffffu, leaf)) {
-        int k0 = (-ref - 1) * P.L;
-        int k1 = min(k0 + P.L, P.n_prims);
-        if (leaf) {
-            for (int k = k0; k < k1; ++k) {
-                float y, w;
-                float3 v;
-                leaf_term<KINDS, GRAD>(P, q, k, y, w, v);
-                lse_add<GRAD>(acc, y, w, v);
-            }
-            nleaf += k1 - k0;
-        }
+    if (has && lane == leader) ws.lead[owner] = lane;
+    __syncwarp();
+    int src = ws.lead[lane];
+    int sl = src < 0 ? lane : src;
+    float m2 = __shfl_sync(0xffffffffu, tm, sl), s2 = __shfl_sync(0xffffffffu, ts, sl);
+    float x2 = 0.f, y2 = 0.f, z2 = 0.f;
+    if (GRAD) {
+        x2 = __shfl_sync(0xffffffffu, tx, sl);
+        y2 = __shfl_sync(0xffffffffu, ty, sl);
+        z2 = __shfl_sync(0xffffffffu, tz, sl);
     }
-    unsigned pm = __ballot_sync(0xffffffffu, need);
-    if (pm) {
-        if (sp < PK_STACK) {
-            if (lane == 0) st[sp] = make_int2(ref, (int)pm);
-            ++sp;
-        } else {
-            overflow = true;
+    if (src >= 0) {
+        lse_merge<GRAD>(acc, m2, s2, x2, y2, z2);
+        ws.lead[lane] = -1;
+    }
+    __syncwarp();
+}
+
+// queue the leaf bucket `ref` for the lanes in `lm`, flushing full groups of 32
+template <int KINDS, bool GRAD>
+__device__ __forceinline__ void queue_leaf(const SdParams& P, float3 q, bool leaf, unsigned lm, int ref, Lse& acc,
+                                           const WarpShared& ws, int& nq, int lane, int& nleaf)
+{
+    int k0 = (-ref - 1) * P.L;
+    int k1 = min(k0 + P.L, P.n_prims);
+    unsigned lt = (1u << lane) - 1u;
+    int cnt = __popc(lm);
+    if (leaf) nleaf += k1 - k0;
+    for (int k = k0; k < k1; ++k) {
+        if (leaf) ws.queue[nq + __popc(lm & lt)] = make_int2(lane, k);
+        nq += cnt;
+        if (nq >= 32) {
+            nq -= 32;
+            flush_queue<KINDS, GRAD>(P, q, ws.queue + nq, 32, ws, lane, acc);
         }
     }
 }
 
-template <int KINDS, bool GRAD>
+// Both children of one record, for every lane of the packet at once. The two
+// Barnes-Hut tests run as packed two-wide fp32 operations whose per-element
+// rounding equals the scalar test (lo - q = lo + (-q), q - hi = q + (-hi));
+// both far-field terms of App. D (n_B w_B e^{-alpha d} with direction
+// (q - y_B)/d) are added without branches. Returns the lane masks of the
+// children that must be opened.
+template <int KINDS, bool GRAD, bool COUNT>
+__device__ __forceinline__ void packet_record(const SdParams& P, float3 q, float3 nq3, bool mine, int rec, Lse& acc,
+                                              const WarpShared& ws, int& nq, int lane, int& ntest, int& nfar,
+                                              int& nleaf, int& ref0, int& ref1, unsigned& open0, unsigned& open1)
+{
+    const SdNode& r = P.nodes[rec];
+    float4 a = __ldg(&r.a), b = __ldg(&r.b), c = __ldg(&r.c);
+    int4 d = __ldg(&r.d);
+    float2 nw = __ldg(&P.nw2[rec]);
+    const bool has1 = d.y != SD_NO_CHILD;
+    float2 ax = __fadd2_rn(make_float2(a.x, a.y), make_float2(nq3.x, nq3.x));
+    float2 ay = __fadd2_rn(make_float2(a.z, a.w), make_float2(nq3.y, nq3.y));
+    float2 az = __fadd2_rn(make_float2(b.x, b.y), make_float2(nq3.z, nq3.z));
+    float2 bx = __fadd2_rn(make_float2(q.x, q.x), make_float2(b.z, b.w));
+    float2 by = __fadd2_rn(make_float2(q.y, q.y), make_float2(c.x, c.y));
+    float2 bz = __fadd2_rn(make_float2(q.z, q.z), make_float2(c.z, c.w));
+    float2 dx = make_float2(fmaxf(fmaxf(ax.x, bx.x), 0.f), fmaxf(fmaxf(ax.y, bx.y), 0.f));
+    float2 dy = make_float2(fmaxf(fmaxf(ay.x, by.x), 0.f), fmaxf(fmaxf(ay.y, by.y), 0.f));
+    float2 dz = make_float2(fmaxf(fmaxf(az.x, bz.x), 0.f), fmaxf(fmaxf(az.y, bz.y), 0.f));
+    float2 db = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
+    float2 rhs = __fmul2_rn(make_float2(P.beta2, P.beta2), db);
+    const bool t1 = mine && has1;
+    const bool far0 = mine && __int_as_float(d.z) < rhs.x;
+    const bool far1 = t1 && __int_as_float(d.w) < rhs.y;
+    {
+        float r0 = rsqrtf(db.x), r1 = rsqrtf(db.y);
+        float y0 = far0 ? -P.alpha2 * (db.x * r0) : SD_NEG;
+        float y1 = far1 ? -P.alpha2 * (db.y * r1) : SD_NEG;
+        float w0 = far0 ? nw.x : 0.f;
+        float w1 = far1 ? nw.y : 0.f;
+        float3 v0 = f3(0.f, 0.f, 0.f), v1 = f3(0.f, 0.f, 0.f);
+        if (GRAD) {
+            r0 = far0 ? r0 : 0.f;
+            r1 = far1 ? r1 : 0.f;
+            v0 = f3(copysignf(dx.x, bx.x) * r0, copysignf(dy.x, by.x) * r0, copysignf(dz.x, bz.x) * r0);
+            v1 = f3(copysignf(dx.y, bx.y) * r1, copysignf(dy.y, by.y) * r1, copysignf(dz.y, bz.y) * r1);
+        }
+        lse_add2<GRAD>(acc, y0, w0, v0, y1, w1, v1);
+    }
+    if (COUNT) {
+        ntest += mine ? (has1 ? 2 : 1) : 0;
+        nfar += (far0 ? 1 : 0) + (far1 ? 1 : 0);
+    }
+    const bool near0 = mine && !far0;
+    const bool near1 = t1 && !far1;
+    const unsigned nm0 = __ballot_sync(0xffffffffu, near0);
+    const unsigned nm1 = __ballot_sync(0xffffffffu, near1);
+    ref0 = d.x;
+    ref1 = d.y;
+    open0 = open1 = 0u;
+    if (nm0) {
+        if (d.x < 0) queue_leaf<KINDS, GRAD>(P, q, near0, nm0, d.x, acc, ws, nq, lane, nleaf);
+        else open0 = nm0;
+    }
+    if (nm1) {
+        if (d.y < 0) queue_leaf<KINDS, GRAD>(P, q, near1, nm1, d.y, acc, ws, nq, lane, nleaf);
+        else open1 = nm1;
+    }
+}
+
+template <int KINDS, bool GRAD, bool COUNT>
 __global__ void __launch_bounds__(PK_MAX_THREADS) k_traverse(SdParams P, const float* __restrict__ qs, int M,
                                                              const int* __restrict__ order,
                                                              float* __restrict__ value, float* __restrict__ grad,
-                                                             int* __restrict__ counts, int* __restrict__ status)
+                                                             int* __restrict__ counts, int* __restrict__ status,
+                                                             int* __restrict__ work, int npackets)
 {
-    extern __shared__ int2 stk[];
+    extern __shared__ int smem_i[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    int2* st = stk + wib * PK_STACK;
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    const bool inrange = t < M;
-    int qi = inrange ? (order ? order[t] : t) : 0;
-    float3 q = f3(0.f, 0.f, 0.f);
-    if (inrange) q = f3(qs[3 * qi], qs[3 * qi + 1], qs[3 * qi + 2]);
-    bool ok = inrange && isfinite(q.x) && isfinite(q.y) && isfinite(q.z);
-    if (inrange && !ok) {
-        atomicOr(status, 1 << SD_ERR_NONFINITE);
-        value[qi] = __int_as_float(0x7fffffff);
-        if (grad) grad[3 * qi] = grad[3 * qi + 1] = grad[3 * qi + 2] = __int_as_float(0x7fffffff);
-        if (counts) counts[3 * qi] = counts[3 * qi + 1] = counts[3 * qi + 2] = 0;
-    }
-    unsigned mask = __ballot_sync(0xffffffffu, ok);
-    if (!mask) return;
-    Lse acc;
-    lse_init(acc);
-    int ntest = 0, nfar = 0, nleaf = 0;
-    bool overflow = false;
-    int sp = 0;
-    int rec = P.root_record;
+    int* wbase = smem_i + wib * PK_WARP_INTS;
+    WarpShared ws;
+    ws.stack = reinterpret_cast<int2*>(wbase);
+    ws.queue = reinterpret_cast<int2*>(wbase + 2 * PK_STACK);
+    ws.lead = wbase + 2 * PK_STACK + 2 * PK_QCAP;
+    ws.lead[lane] = -1;
+    __syncwarp();
     for (;;) {
-        const SdNode& r = P.nodes[rec];
-        float4 a = __ldg(&r.a), b = __ldg(&r.b), c = __ldg(&r.c);
-        int4 d = __ldg(&r.d);
-        bool mine = (mask >> lane) & 1u;
-        packet_child<KINDS, GRAD>(P, q, mine, a.x, a.y, a.z, a.w, b.x, b.y, d.x, __int_as_float(d.z), acc, st, sp,
-                                  lane, ntest, nfar, nleaf, overflow);
-        if (d.y != SD_NO_CHILD)
-            packet_child<KINDS, GRAD>(P, q, mine, b.z, b.w, c.x, c.y, c.z, c.w, d.y, __int_as_float(d.w), acc, st,
-                                      sp, lane, ntest, nfar, nleaf, overflow);
-        if (sp == 0) break;
-        __syncwarp();
-        int2 e = st[--sp];
-        __syncwarp();
-        rec = e.x;
-        mask = (unsigned)e.y;
-    }
-    if (overflow && lane == 0) atomicOr(status, 1 << SD_ERR_TOO_LARGE);
-    if (!ok) return;
-    // Alg. 2: d^ = -log(c)/alpha, grad d^ = grad c / c (c >= 1 after the shift)
-    value[qi] = -(acc.m + sd_lg2(acc.s)) * P.inv_alpha2;
-    if (GRAD) {
-        float is = 1.f / acc.s;
-        grad[3 * qi] = acc.gx * is;
-        grad[3 * qi + 1] = acc.gy * is;
-        grad[3 * qi + 2] = acc.gz * is;
-    }
-    if (counts) {
-        counts[3 * qi] = ntest;
-        counts[3 * qi + 1] = nfar;
-        counts[3 * qi + 2] = nleaf;
+        int pkt = 0;
+        if (lane == 0) pkt = atomicAdd(work, 1);
+        pkt = __shfl_sync(0xffffffffu, pkt, 0);
+        if (pkt >= npackets) break;
+        const int t = pkt * 32 + lane;
+        const bool inrange = t < M;
+        int qi = inrange ? (order ? order[t] : t) : 0;
+        float3 q = f3(0.f, 0.f, 0.f);
+        if (inrange) q = f3(qs[3 * qi], qs[3 * qi + 1], qs[3 * qi + 2]);
+        bool ok = inrange && isfinite(q.x) && isfinite(q.y) && isfinite(q.z);
+        if (inrange && !ok) {
+            atomicOr(status, 1 << SD_ERR_NONFINITE);
+            value[qi] = __int_as_float(0x7fffffff);
+            if (grad) grad[3 * qi] = grad[3 * qi + 1] = grad[3 * qi + 2] = __int_as_float(0x7fffffff);
+            if (counts) counts[3 * qi] = counts[3 * qi + 1] = counts[3 * qi + 2] = 0;
+        }
+        if (!ok) q = f3(0.f, 0.f, 0.f);
+        unsigned mask = __ballot_sync(0xffffffffu, ok);
+        if (!mask) continue;
+        Lse acc;
+        acc.m = SD_NEG; acc.s = 0.f; acc.gx = acc.gy = acc.gz = 0.f;
+        int ntest = 0, nfar = 0, nleaf = 0;
+        bool overflow = false;
+        int sp = 0, nq = 0;
+        int rec = P.root_record;
+        const float3 nq3 = f3(-q.x, -q.y, -q.z);
+        for (;;) {
+            const bool mine = (mask >> lane) & 1u;
+            int r0, r1;
+            unsigned o0, o1;
+            packet_record<KINDS, GRAD, COUNT>(P, q, nq3, mine, rec, acc, ws, nq, lane, ntest, nfar, nleaf, r0, r1,
+                                              o0, o1);
+            // descend into a child that must be opened; keep the other on the stack
+            if (o0) {
+                if (o1) {
+                    if (sp < PK_STACK) {
+                        if (lane == 0) ws.stack[sp] = make_int2(r1, (int)o1);
+                        ++sp;
+                    } else {
+                        overflow = true;
+                        break;
+                    }
+                }
+                rec = r0;
+                mask = o0;
+                continue;
+            }
+            if (o1) {
+                rec = r1;
+                mask = o1;
+                continue;
+            }
+            if (sp == 0) break;
+            __syncwarp();
+            int2 e = ws.stack[--sp];
+            __syncwarp();
+            rec = e.x;
+            mask = (unsigned)e.y;
+        }
+        if (nq > 0) flush_queue<KINDS, GRAD>(P, q, ws.queue, nq, ws, lane, acc);
+        if (overflow && lane == 0) atomicOr(status, 1 << SD_ERR_TOO_LARGE);
+        if (!ok) continue;
+        // Alg. 2: d^ = -log(c)/alpha, grad d^ = grad c / c (c >= 1 after the shift)
+        value[qi] = -(acc.m + sd_lg2(acc.s)) * P.inv_alpha2;
+        if (GRAD) {
+            float is = 1.f / acc.s;
+            grad[3 * qi] = acc.gx * is;
+            grad[3 * qi + 1] = acc.gy * is;
+            grad[3 * qi + 2] = acc.gz * is;
+        }
+        if (COUNT) {
+            counts[3 * qi] = ntest;
+            counts[3 * qi + 1] = nfar;
+            counts[3 * qi + 2] = nleaf;
+        }
     }
 }
 
@@ -226,40 +368,66 @@ __global__ void k_query_codes(const float* __restrict__ qs, int M, float3 lo, fl
     vals[t] = t;
 }
 
+int sm_count()
+{
+    static int cached[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) dev = 0;
+    if (!cached[dev]) {
+        int v = 0;
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        cached[dev] = v > 0 ? v : 1;
+    }
+    return cached[dev];
+}
+
 template <bool BRUTE, int KINDS, bool GRAD>
 void launch_one(const sd_tree* t, const float* q, int M, const int* order, float* value, float* grad, int* counts,
-                int block, cudaStream_t st)
+                int block, int* work, cudaStream_t st)
 {
     if (BRUTE) {
         k_brute<KINDS, GRAD><<<(M + BT - 1) / BT, BT, 0, st>>>(t->P, q, M, value, grad, t->status);
     } else {
         int B = block > 0 ? block : 128;
-        size_t smem = sizeof(int2) * PK_STACK * (B / 32);
-        k_traverse<KINDS, GRAD><<<(M + B - 1) / B, B, smem, st>>>(t->P, q, M, order, value, grad, counts, t->status);
+        size_t smem = sizeof(int) * PK_WARP_INTS * (B / 32);
+        int npackets = (M + 31) / 32;
+        int per_sm = 0;
+        if (counts) {
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_traverse<KINDS, GRAD, true>, B, smem);
+            int blocks = std::max(1, std::min(per_sm * sm_count(), (npackets * 32 + B - 1) / B));
+            k_traverse<KINDS, GRAD, true><<<blocks, B, smem, st>>>(t->P, q, M, order, value, grad, counts,
+                                                                   t->status, work, npackets);
+        } else {
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_traverse<KINDS, GRAD, false>, B, smem);
+            int blocks = std::max(1, std::min(per_sm * sm_count(), (npackets * 32 + B - 1) / B));
+            k_traverse<KINDS, GRAD, false><<<blocks, B, smem, st>>>(t->P, q, M, order, value, grad, counts,
+                                                                    t->status, work, npackets);
+        }
     }
 }
 
 template <bool BRUTE>
 void dispatch(const sd_tree* t, const float* q, int M, const int* order, float* value, float* grad, int* counts,
-              int block, cudaStream_t st)
+              int block, int* work, cudaStream_t st)
 {
     bool g = grad != nullptr;
     switch (t->kinds) {
     case SD_HAS_PTS:
-        g ? launch_one<BRUTE, SD_HAS_PTS, true>(t, q, M, order, value, grad, counts, block, st)
-          : launch_one<BRUTE, SD_HAS_PTS, false>(t, q, M, order, value, grad, counts, block, st);
+        g ? launch_one<BRUTE, SD_HAS_PTS, true>(t, q, M, order, value, grad, counts, block, work, st)
+          : launch_one<BRUTE, SD_HAS_PTS, false>(t, q, M, order, value, grad, counts, block, work, st);
         break;
     case SD_HAS_SEGS:
-        g ? launch_one<BRUTE, SD_HAS_SEGS, true>(t, q, M, order, value, grad, counts, block, st)
-          : launch_one<BRUTE, SD_HAS_SEGS, false>(t, q, M, order, value, grad, counts, block, st);
+        g ? launch_one<BRUTE, SD_HAS_SEGS, true>(t, q, M, order, value, grad, counts, block, work, st)
+          : launch_one<BRUTE, SD_HAS_SEGS, false>(t, q, M, order, value, grad, counts, block, work, st);
         break;
     case SD_HAS_TRIS:
-        g ? launch_one<BRUTE, SD_HAS_TRIS, true>(t, q, M, order, value, grad, counts, block, st)
-          : launch_one<BRUTE, SD_HAS_TRIS, false>(t, q, M, order, value, grad, counts, block, st);
+        g ? launch_one<BRUTE, SD_HAS_TRIS, true>(t, q, M, order, value, grad, counts, block, work, st)
+          : launch_one<BRUTE, SD_HAS_TRIS, false>(t, q, M, order, value, grad, counts, block, work, st);
         break;
     default:
-        g ? launch_one<BRUTE, 7, true>(t, q, M, order, value, grad, counts, block, st)
-          : launch_one<BRUTE, 7, false>(t, q, M, order, value, grad, counts, block, st);
+        g ? launch_one<BRUTE, 7, true>(t, q, M, order, value, grad, counts, block, work, st)
+          : launch_one<BRUTE, 7, false>(t, q, M, order, value, grad, counts, block, work, st);
         break;
     }
 }
@@ -337,18 +505,23 @@ extern "C" int sd_query(const sd_tree* t, const float* q, int64_t M, float* valu
         return sd_cuda_status(cudaGetLastError());
     }
     const int* order = opts.order;
+    bool sort = !order && opts.sort_queries && m > 1;
+    // scratch: the packet counter, then the traversal order if it is computed here
     void* tmp = nullptr;
-    if (!order && opts.sort_queries && m > 1) {
-        cudaError_t e = cudaMallocAsync(&tmp, sizeof(int) * (size_t)m, st);
-        if (e != cudaSuccess) { cudaGetLastError(); return SD_ERR_OOM; }
-        rc = compute_order(t, q, m, (int32_t*)tmp, st);
+    cudaError_t e = cudaMallocAsync(&tmp, 256 + (sort ? sizeof(int) * (size_t)m : 0), st);
+    if (e != cudaSuccess) { cudaGetLastError(); return SD_ERR_OOM; }
+    int* work = (int*)tmp;
+    cudaMemsetAsync(work, 0, sizeof(int), st);
+    if (sort) {
+        int32_t* ord = (int32_t*)((char*)tmp + 256);
+        rc = compute_order(t, q, m, ord, st);
         if (rc != SD_OK) { cudaFreeAsync(tmp, st); return rc; }
-        order = (const int*)tmp;
+        order = ord;
     }
-    dispatch<false>(t, q, m, order, value, grad, opts.counts, opts.block, st);
+    dispatch<false>(t, q, m, order, value, grad, opts.counts, opts.block, work, st);
     sd_count_launches(1);
-    cudaError_t e = cudaGetLastError();
-    if (tmp) cudaFreeAsync(tmp, st);
+    e = cudaGetLastError();
+    cudaFreeAsync(tmp, st);
     return sd_cuda_status(e);
 }
 
@@ -366,7 +539,7 @@ extern "C" int sd_query_brute(const sd_tree* t, const float* q, int64_t M, float
         sd_count_launches(1);
         return sd_cuda_status(cudaGetLastError());
     }
-    dispatch<true>(t, q, m, nullptr, value, grad, nullptr, 0, st);
+    dispatch<true>(t, q, m, nullptr, value, grad, nullptr, 0, nullptr, st);
     sd_count_launches(1);
     return sd_cuda_status(cudaGetLastError());
 }
