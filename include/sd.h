@@ -109,7 +109,7 @@ int sd_query(const sd_tree* t, const float* q, int64_t M, float* value, float* g
 
 /*
  * Traversal order for sd_query: writes to `order` (device [M] int32) the
- * query indices sorted by the 30-bit Morton code of each query relative to
+ * query indices sorted by the 24-bit Morton code of each query relative to
  * the tree's scene box (stable; ties keep index order). Asynchronous on
  * `stream`; uses stream-ordered temporary device memory.
  */

@@ -51,13 +51,17 @@ struct Geo {
     int n;
 };
 
-// vertex j (0..2) of primitive i, as fp32 xyz
+__device__ __forceinline__ int clampi(int v, int n) { return min(max(v, 0), n - 1); }
+
+// vertex j (0..2) of primitive i, as fp32 xyz. Indices are clamped into
+// range: an out-of-range index is reported by the validation kernels and the
+// build is discarded, but no kernel ever reads outside the inputs.
 __device__ __forceinline__ float3 prim_vertex(const Geo& g, int i, int j)
 {
     const float* p;
     if (i < g.np) p = g.P + 3 * i;
-    else if (i < g.np + g.ne) p = g.EV + 3 * g.E[2 * (i - g.np) + j];
-    else p = g.TV + 3 * g.F[3 * (i - g.np - g.ne) + j];
+    else if (i < g.np + g.ne) p = g.EV + 3 * clampi(g.E[2 * (i - g.np) + j], g.nev);
+    else p = g.TV + 3 * clampi(g.F[3 * (i - g.np - g.ne) + j], g.ntv);
     return make_float3(p[0], p[1], p[2]);
 }
 __device__ __forceinline__ int prim_nv(const Geo& g, int i) { return i < g.np ? 1 : (i < g.np + g.ne ? 2 : 3); }
@@ -101,10 +105,12 @@ __global__ void k_check_index(const int* __restrict__ idx, int64_t count, int nv
 }
 
 // --- incidence counts (App. C.2, C.3): one count per incidence slot -------
-__global__ void k_count_slots(const int* __restrict__ idx, int64_t count, int* __restrict__ cnt)
+__global__ void k_count_slots(const int* __restrict__ idx, int64_t count, int nv, int* __restrict__ cnt)
 {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
-        atomicAdd(&cnt[idx[i]], 1);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+        int v = idx[i];
+        if (v >= 0 && v < nv) atomicAdd(&cnt[v], 1);
+    }
 }
 
 __device__ __forceinline__ unsigned long long edge_key(int a, int b)
@@ -148,14 +154,14 @@ __device__ __forceinline__ int edge_lookup(const unsigned long long* keys, const
 }
 
 // triangle i: v_i = max vertex valence, e_i = max edge valence -> (1/v_i, 1/e_i)
-__global__ void k_tri_params(const int* __restrict__ F, int nf, const int* __restrict__ vcnt,
+__global__ void k_tri_params(const int* __restrict__ F, int nf, int ntv, const int* __restrict__ vcnt,
                              const unsigned long long* keys, const int* counts, unsigned mask,
                              float* __restrict__ params, int first, BuildScalars* bs)
 {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= nf) return;
-    int a = F[3 * t], b = F[3 * t + 1], c = F[3 * t + 2];
-    int vm = max(vcnt[a], max(vcnt[b], vcnt[c]));
+    int a = clampi(F[3 * t], ntv), b = clampi(F[3 * t + 1], ntv), c = clampi(F[3 * t + 2], ntv);
+    int vm = max(max(vcnt[a], max(vcnt[b], vcnt[c])), 1);
     int em = max(edge_lookup(keys, counts, mask, edge_key(a, b)),
                  max(edge_lookup(keys, counts, mask, edge_key(b, c)), edge_lookup(keys, counts, mask, edge_key(c, a))));
     params[2 * (first + t)] = 1.f / (float)vm;
@@ -164,12 +170,12 @@ __global__ void k_tri_params(const int* __restrict__ F, int nf, const int* __res
 }
 
 // edge i: (u, v) = (1/|N_i0|, 1/|N_i1|)
-__global__ void k_edge_params(const int* __restrict__ E, int ne, const int* __restrict__ cnt,
+__global__ void k_edge_params(const int* __restrict__ E, int ne, int nev, const int* __restrict__ cnt,
                               float* __restrict__ params, int first, BuildScalars* bs)
 {
     int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= ne) return;
-    int c0 = cnt[E[2 * e]], c1 = cnt[E[2 * e + 1]];
+    int c0 = max(cnt[clampi(E[2 * e], nev)], 1), c1 = max(cnt[clampi(E[2 * e + 1], nev)], 1);
     params[2 * (first + e)] = 1.f / (float)c0;
     params[2 * (first + e) + 1] = 1.f / (float)c1;
     atomicMax(&bs->A_E, max(c0, c1));
@@ -470,7 +476,7 @@ extern "C" int sd_build(const sd_geometry* g, float alpha, float beta, const sd_
     size_t o_params = carve(sizeof(float) * 2 * std::max(n, 1));
     size_t o_status = carve(sizeof(int) * 4);
     t->mem_bytes = off;
-    cudaError_t ce = cudaMalloc(&t->mem, off);
+    cudaError_t ce = cudaMallocAsync(&t->mem, off, st);
     if (ce != cudaSuccess) { delete t; cudaGetLastError(); return SD_ERR_OOM; }
     char* base = (char*)t->mem;
     t->nodes = (SdNode*)(base + o_nodes);
@@ -546,41 +552,27 @@ extern "C" int sd_build(const sd_geometry* g, float alpha, float beta, const sd_
     if (geo.ntv) { ++nl; k_vertices<<<std::min(nblk(geo.ntv, T), 1024), T, 0, st>>>(geo.TV, geo.ntv, bs); }
     if (geo.ne) { ++nl; k_check_index<<<std::min(nblk(2 * (int64_t)geo.ne, T), 1024), T, 0, st>>>(geo.E, 2 * (int64_t)geo.ne, geo.nev, bs); }
     if (geo.nf) { ++nl; k_check_index<<<std::min(nblk(3 * (int64_t)geo.nf, T), 1024), T, 0, st>>>(geo.F, 3 * (int64_t)geo.nf, geo.ntv, bs); }
-    // the index checks must pass before any kernel dereferences an index
-    BuildScalars hb;
-    cudaMemcpyAsync(&hb, bs, sizeof(hb), cudaMemcpyDeviceToHost, st);
-    ce = cudaStreamSynchronize(st);
-    int status = SD_OK;
-    if (ce != cudaSuccess) status = sd_cuda_status(ce);
-    else if (hb.status & ST_INDEX) status = SD_ERR_INDEX;
-    else if (hb.status & ST_NONFINITE) status = SD_ERR_NONFINITE;
-    if (status != SD_OK) {
-        sd_count_launches(nl);
-        cudaFreeAsync(tmp, st);
-        cudaStreamSynchronize(st);
-        cudaFree(t->mem);
-        delete t;
-        return status;
-    }
+    // validation results are read once, at the end of the build; the kernels
+    // below clamp every index they dereference
 
     // incidence counts and weight parameters
     if (geo.ne) {
         cudaMemsetAsync(ecnt, 0, sizeof(int) * geo.nev, st);
         ++nl;
-        k_count_slots<<<std::min(nblk(2 * (int64_t)geo.ne, T), 4096), T, 0, st>>>(geo.E, 2 * (int64_t)geo.ne, ecnt);
+        k_count_slots<<<std::min(nblk(2 * (int64_t)geo.ne, T), 4096), T, 0, st>>>(geo.E, 2 * (int64_t)geo.ne, geo.nev, ecnt);
         ++nl;
-        k_edge_params<<<nblk(geo.ne, T), T, 0, st>>>(geo.E, geo.ne, ecnt, t->params, geo.np, bs);
+        k_edge_params<<<nblk(geo.ne, T), T, 0, st>>>(geo.E, geo.ne, geo.nev, ecnt, t->params, geo.np, bs);
     }
     if (geo.nf) {
         cudaMemsetAsync(vcnt, 0, sizeof(int) * geo.ntv, st);
         cudaMemsetAsync(hkeys, 0xff, sizeof(unsigned long long) * hcap, st);
         cudaMemsetAsync(hcnt, 0, sizeof(int) * hcap, st);
         ++nl;
-        k_count_slots<<<std::min(nblk(3 * (int64_t)geo.nf, T), 4096), T, 0, st>>>(geo.F, 3 * (int64_t)geo.nf, vcnt);
+        k_count_slots<<<std::min(nblk(3 * (int64_t)geo.nf, T), 4096), T, 0, st>>>(geo.F, 3 * (int64_t)geo.nf, geo.ntv, vcnt);
         ++nl;
         k_edge_insert<<<nblk(3 * (int64_t)geo.nf, T), T, 0, st>>>(geo.F, geo.nf, hkeys, hcnt, hcap - 1);
         ++nl;
-        k_tri_params<<<nblk(geo.nf, T), T, 0, st>>>(geo.F, geo.nf, vcnt, hkeys, hcnt, hcap - 1, t->params,
+        k_tri_params<<<nblk(geo.nf, T), T, 0, st>>>(geo.F, geo.nf, geo.ntv, vcnt, hkeys, hcnt, hcap - 1, t->params,
                                                      geo.np + geo.ne, bs);
     }
     if (n > 0) {
@@ -606,15 +598,20 @@ extern "C" int sd_build(const sd_geometry* g, float alpha, float beta, const sd_
         ++nl;
         k_gather<<<nblk(n, T), T, 0, st>>>(geo, sv, t->params, t->hdr, t->ext);
     }
+    BuildScalars hb;
     cudaMemcpyAsync(&hb, bs, sizeof(hb), cudaMemcpyDeviceToHost, st);
     cudaFreeAsync(tmp, st);
     sd_count_launches(nl);
     ce = cudaStreamSynchronize(st);
     if (ce == cudaSuccess) ce = cudaGetLastError();
-    if (ce != cudaSuccess) {
+    int status = SD_OK;
+    if (ce != cudaSuccess) status = sd_cuda_status(ce);
+    else if (hb.status & ST_INDEX) status = SD_ERR_INDEX;
+    else if (hb.status & ST_NONFINITE) status = SD_ERR_NONFINITE;
+    if (status != SD_OK) {
         cudaFree(t->mem);
         delete t;
-        return sd_cuda_status(ce);
+        return status;
     }
 
     sd_tree_info& inf = t->info;

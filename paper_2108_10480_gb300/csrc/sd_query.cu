@@ -346,8 +346,9 @@ __global__ void k_fill_empty(float* value, float* grad, int M)
     if (grad) grad[3 * t] = grad[3 * t + 1] = grad[3 * t + 2] = 0.f;
 }
 
-// 30-bit Morton code of each query relative to the scene box (clamped), the
-// traversal order
+// 24-bit Morton code of each query relative to the scene box (clamped), the
+// traversal order (8 bits per axis already give cells far smaller than a
+// packet's footprint; the order changes speed only, never results)
 __global__ void k_query_codes(const float* __restrict__ qs, int M, float3 lo, float3 inv_ext,
                               unsigned* __restrict__ keys, int* __restrict__ vals)
 {
@@ -359,10 +360,10 @@ __global__ void k_query_codes(const float* __restrict__ qs, int M, float3 lo, fl
     for (int j = 0; j < 3; ++j) {
         float u = (c[j] - l[j]) * ie[j];
         u = fminf(fmaxf(u, 0.f), 1.f);          // NaN -> 0
-        k[j] = min((unsigned)(u * 1024.f), 1023u);
+        k[j] = min((unsigned)(u * 256.f), 255u);
     }
     unsigned code = 0;
-    for (int b = 9; b >= 0; --b)
+    for (int b = 7; b >= 0; --b)
         code = (code << 3) | (((k[0] >> b) & 1u) << 2) | (((k[1] >> b) & 1u) << 1) | ((k[2] >> b) & 1u);
     keys[t] = code;
     vals[t] = t;
@@ -463,7 +464,7 @@ int compute_order(const sd_tree* t, const float* q, int m, int32_t* order, cudaS
     float3 ie = make_float3(ex[0] > 0 ? 1.f / ex[0] : 0.f, ex[1] > 0 ? 1.f / ex[1] : 0.f, ex[2] > 0 ? 1.f / ex[2] : 0.f);
     int nl = 1;
     k_query_codes<<<(m + 255) / 256, 256, 0, st>>>(q, m, lo, ie, k0, order);
-    int where = sdsort::sort_pairs<unsigned, int>(k0, order, k1, v1, m, 30, hist, st, &nl);
+    int where = sdsort::sort_pairs<unsigned, int>(k0, order, k1, v1, m, 24, hist, st, &nl);
     if (where) cudaMemcpyAsync(order, v1, sizeof(int) * (size_t)m, cudaMemcpyDeviceToDevice, st);
     sd_count_launches(nl);
     e = cudaGetLastError();

@@ -1,7 +1,7 @@
 // Stable LSD radix sort (8-bit digits) of key/value pairs in device memory.
-// Per pass: a per-tile digit histogram, one exclusive scan over
-// (digit, tile), and a stable scatter that ranks equal digits inside a tile
-// with warp match masks. Used for the Morton order of primitives (64-bit
+// Per pass: a per-tile digit histogram (plus digit totals), an exclusive
+// scan over (digit, tile) with one block per digit, and a stable scatter
+// that ranks equal digits inside a tile with warp match masks. Used for the Morton order of primitives (64-bit
 // keys) and of queries (32-bit keys).
 #pragma once
 
@@ -11,48 +11,79 @@
 namespace sdsort {
 
 constexpr int THREADS = 256;
-constexpr int ITEMS = 16;
+constexpr int ITEMS = 4;
 constexpr int TILE = THREADS * ITEMS;
 constexpr int WARPS = THREADS / 32;
 
 template <typename K>
 __global__ void __launch_bounds__(THREADS) hist_kernel(const K* __restrict__ keys, int n, int shift,
-                                                       uint32_t* __restrict__ hist, int ntiles)
+                                                       uint32_t* __restrict__ hist, int ntiles,
+                                                       uint32_t* __restrict__ tot)
 {
     __shared__ uint32_t h[256];
     h[threadIdx.x] = 0;
     __syncthreads();
     int base = blockIdx.x * TILE;
-#pragma unroll 4
+#pragma unroll
     for (int r = 0; r < ITEMS; ++r) {
         int i = base + r * THREADS + threadIdx.x;
         if (i < n) atomicAdd(&h[(unsigned)(keys[i] >> shift) & 255u], 1u);
     }
     __syncthreads();
-    hist[threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
+    uint32_t c = h[threadIdx.x];
+    hist[threadIdx.x * ntiles + blockIdx.x] = c;
+    if (c) atomicAdd(&tot[threadIdx.x], c);
 }
 
-// exclusive scan of `total` counters with one block of 1024 threads
-static __global__ void __launch_bounds__(1024) scan_kernel(uint32_t* __restrict__ a, int total)
+// Exclusive scan of the (digit, tile) counters, one block per digit: the
+// digit's base is the sum of the totals of all smaller digits, and the
+// block scans its row of per-tile counts (contiguous in memory).
+static __global__ void __launch_bounds__(256) scan_rows_kernel(uint32_t* __restrict__ hist, int ntiles,
+                                                              const uint32_t* __restrict__ tot)
 {
-    __shared__ uint32_t part[1024];
-    int per = (total + 1023) / 1024;
-    int b = threadIdx.x * per, e = min(b + per, total);
-    uint32_t s = 0;
-    for (int i = b; i < e; ++i) s += a[i];
-    part[threadIdx.x] = s;
-    __syncthreads();
-    for (int off = 1; off < 1024; off <<= 1) {
-        uint32_t v = threadIdx.x >= off ? part[threadIdx.x - off] : 0u;
-        __syncthreads();
-        part[threadIdx.x] += v;
-        __syncthreads();
+    __shared__ uint32_t wsum[8];
+    __shared__ uint32_t sbase;
+    const int d = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (warp == 0) {
+        uint32_t acc = 0;
+        for (int k = lane; k < d; k += 32) acc += tot[k];
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) sbase = acc;
     }
-    uint32_t run = part[threadIdx.x] - s;
-    for (int i = b; i < e; ++i) {
-        uint32_t v = a[i];
-        a[i] = run;
-        run += v;
+    __syncthreads();
+    uint32_t carry = sbase;
+    uint32_t* row = hist + (size_t)d * ntiles;
+    for (int c0 = 0; c0 < ntiles; c0 += 256 * 8) {
+        int b = c0 + tid * 8;
+        uint32_t v[8];
+        uint32_t s = 0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            v[k] = (b + k < ntiles) ? row[b + k] : 0u;
+            s += v[k];
+        }
+        uint32_t x = s;
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wsum[warp] = x;
+        __syncthreads();
+        uint32_t wpre = 0, total = 0;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) {
+            uint32_t ws = wsum[w];
+            if (w < warp) wpre += ws;
+            total += ws;
+        }
+        uint32_t run = carry + wpre + x - s;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            if (b + k < ntiles) row[b + k] = run;
+            run += v[k];
+        }
+        carry += total;
+        __syncthreads();
     }
 }
 
@@ -98,7 +129,8 @@ __global__ void __launch_bounds__(THREADS) scatter_kernel(const K* __restrict__ 
     }
 }
 
-inline size_t hist_words(int n) { return (size_t)256 * (size_t)((n + TILE - 1) / TILE); }
+// counters for one sort: per-(digit, tile) counts, then 8 x 256 digit totals
+inline size_t hist_words(int n) { return (size_t)256 * (size_t)((n + TILE - 1) / TILE) + 8 * 256; }
 
 // Sorts (k0, v0) by the low `bits` bits of the key (a multiple of 8 is not
 // required; passes cover ceil(bits / 8) digits). Uses (k1, v1) as the
@@ -111,6 +143,8 @@ int sort_pairs(K* k0, V* v0, K* k1, V* v1, int n, int bits, uint32_t* hist, cuda
     if (n <= 1) return 0;
     int ntiles = (n + TILE - 1) / TILE;
     int passes = (bits + 7) / 8;
+    uint32_t* tot = hist + (size_t)256 * ntiles;
+    cudaMemsetAsync(tot, 0, sizeof(uint32_t) * 256 * passes, st);
     int cur = 0;
     for (int p = 0; p < passes; ++p) {
         int shift = 8 * p;
@@ -118,8 +152,8 @@ int sort_pairs(K* k0, V* v0, K* k1, V* v1, int n, int bits, uint32_t* hist, cuda
         const V* vi = cur ? v1 : v0;
         K* ko = cur ? k0 : k1;
         V* vo = cur ? v0 : v1;
-        hist_kernel<K><<<ntiles, THREADS, 0, st>>>(ki, n, shift, hist, ntiles);
-        scan_kernel<<<1, 1024, 0, st>>>(hist, 256 * ntiles);
+        hist_kernel<K><<<ntiles, THREADS, 0, st>>>(ki, n, shift, hist, ntiles, tot + 256 * p);
+        scan_rows_kernel<<<256, 256, 0, st>>>(hist, ntiles, tot + 256 * p);
         scatter_kernel<K, V><<<ntiles, THREADS, 0, st>>>(ki, vi, ko, vo, n, shift, hist, ntiles);
         cur ^= 1;
         *launches += 3;
