@@ -123,6 +123,23 @@ int sd_query_order(const sd_tree* t, const float* q, int64_t M, int32_t* order, 
 int sd_query_brute(const sd_tree* t, const float* q, int64_t M, float* value, float* grad,
                    const sd_query_opts* opts, void* stream);
 
+/*
+ * sd_query without any device allocation by the library (the paper has no
+ * counterpart; this is an integration entry point). For callers that own a
+ * fixed device-memory budget and must not let a library call cudaMalloc
+ * during their work, where an allocation could block on the device or fail
+ * part-way. Same inputs and outputs as sd_query with default options
+ * (Morton-ordered traversal, value and gradient, no counts).
+ *   M      0 <= M <= 262144 (SD_ERR_TOO_LARGE beyond, nothing launched)
+ * Its temporary storage (about 4.5 MB) is one static device array that
+ * every device loading the library keeps until the process exits. All
+ * calls on a device share it, so calls that overlap on the GPU race; calls
+ * ordered on one stream are safe. The first call on a device looks up the
+ * array's address with that device current: make it before any stream
+ * capture.
+ */
+int sd_query_noalloc(const sd_tree* t, const float* q, int64_t M, float* value, float* grad, void* stream);
+
 /* Synchronise `stream`, return and clear the tree's device status word. */
 int sd_query_status(const sd_tree* t, void* stream);
 

@@ -66,6 +66,7 @@ SIGNATURES = {
     "sd_query_brute": (ctypes.c_int, [c_void_p, c_void_p, c_int64, c_void_p, c_void_p,
                                       ctypes.POINTER(SdQueryOpts), c_void_p]),
     "sd_query_order": (ctypes.c_int, [c_void_p, c_void_p, c_int64, c_void_p, c_void_p]),
+    "sd_query_noalloc": (ctypes.c_int, [c_void_p, c_void_p, c_int64, c_void_p, c_void_p, c_void_p]),
     "sd_query_status": (ctypes.c_int, [c_void_p, c_void_p]),
     "sd_kernel_launches": (ctypes.c_int64, []),
     "sd_tree_get_info": (ctypes.c_int, [c_void_p, ctypes.POINTER(SdTreeInfo)]),

@@ -12,6 +12,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "sd_common.cuh"
 #include "sd_sort.cuh"
@@ -560,4 +561,96 @@ extern "C" int sd_query_status(const sd_tree* t, void* stream)
             if (h & (1 << c)) return c;
     }
     return SD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// sd_query_noalloc: the Barnes-Hut query for callers that must not let this
+// library allocate device memory (for example an application that owns a
+// fixed device-memory budget and forbids allocation during a simulation
+// step, where a cudaMalloc could block on the device or fail part-way).
+// Its temporary storage — the packet counter of the persistent traversal and
+// the buffers of the query Morton sort — lives in one file-scope device
+// array of fixed size, so the call allocates nothing. Limits and sharing:
+//   * at most SD_NOALLOC_MAX_QUERIES queries per call;
+//   * every device that loads this library holds the array until the
+//     process exits;
+//   * all calls on a device share the array and leave their contents in it,
+//     so calls that overlap on the GPU (for example on two streams) race;
+//   * the first call on a device looks up the array's device address once,
+//     with that device current; make that first call before any stream
+//     capture.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int SD_NOALLOC_MAX_QUERIES = 262144;
+constexpr size_t NOALLOC_TILES = (SD_NOALLOC_MAX_QUERIES + sdsort::TILE - 1) / sdsort::TILE;
+constexpr size_t NOALLOC_HIST_WORDS = 256 * NOALLOC_TILES + 8 * 256;
+// [counter: 256 B][keys: 2 x max u32][order, alternate order: 2 x max i32][sort counters]
+constexpr size_t NOALLOC_BYTES = 256 + 4 * sizeof(uint32_t) * (size_t)SD_NOALLOC_MAX_QUERIES +
+                                 sizeof(uint32_t) * NOALLOC_HIST_WORDS;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[64] = {};   // device address of g_noalloc_scratch, per device
+
+}  // namespace
+
+extern "C" int sd_query_noalloc(const sd_tree* t, const float* q, int64_t M, float* value, float* grad,
+                                void* stream)
+{
+    int rc = check_query_args(t, q, M, value);
+    if (rc != SD_OK) return rc;
+    if (M > SD_NOALLOC_MAX_QUERIES) return SD_ERR_TOO_LARGE;
+    if (M == 0) return SD_OK;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return sd_cuda_status(e);
+    if (dev < 0 || dev >= 64) return SD_ERR_INVALID_ARG;
+    char* base = nullptr;
+    {
+        // The array's name is only a host-side stand-in; its device address
+        // is looked up once per device, with that device current.
+        std::lock_guard<std::mutex> lk(g_noalloc_mu);
+        if (!g_noalloc_addr[dev]) {
+            void* p = nullptr;
+            e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+            if (e != cudaSuccess) return sd_cuda_status(e);
+            g_noalloc_addr[dev] = p;
+        }
+        base = (char*)g_noalloc_addr[dev];
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    int m = (int)M;
+    if (t->info.n_prims == 0) {
+        k_fill_empty<<<(m + 255) / 256, 256, 0, st>>>(value, grad, m);
+        sd_count_launches(1);
+        return sd_cuda_status(cudaGetLastError());
+    }
+    int* work = (int*)base;
+    unsigned* k0 = (unsigned*)(base + 256);
+    unsigned* k1 = k0 + SD_NOALLOC_MAX_QUERIES;
+    int* ord0 = (int*)(k1 + SD_NOALLOC_MAX_QUERIES);
+    int* ord1 = ord0 + SD_NOALLOC_MAX_QUERIES;
+    uint32_t* hist = (uint32_t*)(ord1 + SD_NOALLOC_MAX_QUERIES);
+    // the packet counter must start at zero on every call
+    e = cudaMemsetAsync(work, 0, sizeof(int), st);
+    if (e != cudaSuccess) return sd_cuda_status(e);
+    const int* order = nullptr;
+    int nl = 0;
+    if (m > 1) {
+        const sd_tree_info& I = t->info;
+        float3 lo = make_float3(I.scene_lo[0], I.scene_lo[1], I.scene_lo[2]);
+        float ex[3];
+        for (int j = 0; j < 3; ++j) ex[j] = I.scene_hi[j] - I.scene_lo[j];
+        float3 ie = make_float3(ex[0] > 0 ? 1.f / ex[0] : 0.f, ex[1] > 0 ? 1.f / ex[1] : 0.f,
+                                ex[2] > 0 ? 1.f / ex[2] : 0.f);
+        k_query_codes<<<(m + 255) / 256, 256, 0, st>>>(q, m, lo, ie, k0, ord0);
+        ++nl;
+        int where = sdsort::sort_pairs<unsigned, int>(k0, ord0, k1, ord1, m, 24, hist, st, &nl);
+        order = where ? ord1 : ord0;
+    }
+    dispatch<false>(t, q, m, order, value, grad, nullptr, 0, work, st);
+    sd_count_launches(nl + 1);
+    return sd_cuda_status(cudaGetLastError());
 }
