@@ -301,7 +301,52 @@ def _extras(args, c, V, F, q, dev, M):
                   "h2d_bytes_per_step": int(hV.numel() * 4 + hF.numel() * 4 + hq.numel() * 4),
                   "d2h_bytes_per_step": int(hv.numel() * 4 + hg.numel() * 4)}
     res["cpu_baseline"] = _cpu_baseline(c, args)
+    res["pose"] = _pose_leg(args, dev)
     return res
+
+
+def _pose_leg(args, dev, iters=20):
+    """Rigid-body constraint on the street workload: 2,000,000 lidar points +
+    50,000 wire segments (alpha 50, beta 0.5), a 100,002-vertex body, outer
+    LogSumExp alpha_q = 100; one evaluation = placement + Barnes-Hut query of
+    every vertex + outer LSE + pose gradient (sd_pose_query + sd_pose_reduce)."""
+    import torch
+
+    from paper_2108_10480_gb300 import SmoothDistance
+    from paper_2108_10480_gb300 import pose as gp
+    s = synth.config3_scene()
+    b = synth.config3_body()
+    P = torch.from_numpy(s["points"]).to(dev)
+    Vw = torch.from_numpy(s["wire_V"]).to(dev)
+    Ew = torch.from_numpy(s["wire_E"]).to(dev)
+    X0 = torch.from_numpy(b["V0"]).to(dev)
+    pose = np.concatenate([b["theta"], b["p"]])
+    stream = torch.cuda.current_stream()
+    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    for _ in range(2):
+        sd = SmoothDistance(points=P, edges=(Vw, Ew), alpha=50.0, beta=0.5, device=dev)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    sd = SmoothDistance(points=P, edges=(Vw, Ew), alpha=50.0, beta=0.5, device=dev)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    build_ms = e0.elapsed_time(e1)
+    for _ in range(3):
+        X, v, g = gp.pose_query(sd, X0, pose)
+        gp.pose_reduce(X0, v, g, pose, alpha_q=100.0)
+    torch.cuda.synchronize()
+    e1.record(stream)
+    for _ in range(iters):
+        X, v, g = gp.pose_query(sd, X0, pose)
+        out, _ = gp.pose_reduce(X0, v, g, pose, alpha_q=100.0)
+    e2.record(stream)
+    torch.cuda.synchronize()
+    ms = e1.elapsed_time(e2) / iters
+    M = X0.shape[0]
+    return {"what": "street: 2,000,000 points + 50,000 wire segments, 100,002-vertex body; "
+                    "placement + BH query + outer LSE + 6-DoF pose gradient",
+            "build_ms": build_ms, "ms_per_evaluation": ms, "value": M / (ms / 1e3), "unit": "vertex queries/s",
+            "D": float(out[0].item())}
 
 
 def _cpu_baseline(c, args, sample=None):

@@ -140,6 +140,35 @@ int sd_query_brute(const sd_tree* t, const float* q, int64_t M, float* value, fl
  */
 int sd_query_noalloc(const sd_tree* t, const float* q, int64_t M, float* value, float* grad, void* stream);
 
+/*
+ * Rigid-body queries (Sec. 4.5, Eq. opt): places a body's rest vertices by
+ * x_k = R(theta) x0_k + p, theta a rotation vector (exponential map), and
+ * evaluates d^ and grad d^ at every x_k with sd_query.
+ *   X0     device [M,3] rest-pose vertices
+ *   pose   host double[6] = (theta_x, theta_y, theta_z, p_x, p_y, p_z)
+ *   X      device [M,3] output: the placed vertices (the queries)
+ *   value, grad, opts, stream: as for sd_query
+ */
+int sd_pose_query(const sd_tree* t, const float* X0, int64_t M, const double* pose, float* X,
+                  float* value, float* grad, const sd_query_opts* opts, void* stream);
+
+/*
+ * Reduction over a body's vertices and its pose adjoint (Sec. 3.6,
+ * Eq. lse_full2 and Eq. dlse_full for point queries, n(g) = 0, weight 1):
+ *   alpha_q > 0: D = -(1/alpha_q) log sum_k exp(-alpha_q d^_k), gamma_k its
+ *                softmin weights (`gamma` ignored);
+ *   alpha_q <= 0: D = sum_k gamma_k d^_k for the given device [M] gamma
+ *                (an upstream gradient).
+ * Writes device out[7] = (D, dD/dp (3), dD/dtheta (3)) with
+ * dD/dp = sum_k gamma_k g_k and dD/dtheta = J_l(theta)^T sum_k gamma_k
+ * (R x0_k) x g_k (J_l the left Jacobian of SO(3)); if dX0 is not NULL also
+ * device [M,3] dD/dx0_k = gamma_k R^T g_k. value/grad are sd_pose_query's
+ * outputs for the same X0 and pose. The sums are reduced in a fixed order
+ * (deterministic). Uses stream-ordered temporary device memory.
+ */
+int sd_pose_reduce(const float* X0, const float* value, const float* grad, const float* gamma, int64_t M,
+                   const double* pose, float alpha_q, float* out, float* dX0, void* stream);
+
 /* Synchronise `stream`, return and clear the tree's device status word. */
 int sd_query_status(const sd_tree* t, void* stream);
 

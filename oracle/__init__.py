@@ -77,6 +77,7 @@ def _load():
         lib.orc_tree_export.argtypes = [P] * 12
         lib.orc_bh.argtypes = [P, d, d, d, i, i, i, P, i64, P, P, P, P, i]
         lib.orc_bh.restype = i
+        lib.orc_pose_f32.argtypes = [P, P, P, i64, P]
         _lib = lib
         return lib
 

@@ -873,3 +873,22 @@ int orc_bh(void *h, double alpha, double alpha_u, double beta, int paper_metric,
     pthread_mutex_destroy(&p.mu);
     return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* rigid placement of query vertices in fp32                                */
+/* ------------------------------------------------------------------------ */
+/* x_k = R x0_k + p evaluated in fp32 in the fixed order
+   fma(R_i0, x, fma(R_i1, y, R_i2 * z)) + p_i, with R and p rounded to fp32:
+   the query points the GPU path evaluates (Sec. 4.5 places the query mesh by
+   its pose; the rounding rule is part of this project's definition). */
+void orc_pose_f32(const double *R9, const double *p3, const float *X0, int64_t m, float *X)
+{
+    float R[9], p[3];
+    for (int i = 0; i < 9; ++i) R[i] = (float)R9[i];
+    for (int i = 0; i < 3; ++i) p[i] = (float)p3[i];
+    for (int64_t k = 0; k < m; ++k) {
+        float x = X0[3 * k], y = X0[3 * k + 1], z = X0[3 * k + 2];
+        for (int i = 0; i < 3; ++i)
+            X[3 * k + i] = fmaf(R[3 * i], x, fmaf(R[3 * i + 1], y, R[3 * i + 2] * z)) + p[i];
+    }
+}

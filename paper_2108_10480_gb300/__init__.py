@@ -173,3 +173,6 @@ class SmoothDistance:
         _native.check(lib().sd_tree_export(self._h, ctypes.byref(v)), "sd_tree_export")
         t["nb"] = nb
         return t
+
+
+from . import pose  # noqa: E402,F401  (rigid-body constraint and its adjoint)

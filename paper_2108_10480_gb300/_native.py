@@ -67,6 +67,10 @@ SIGNATURES = {
                                       ctypes.POINTER(SdQueryOpts), c_void_p]),
     "sd_query_order": (ctypes.c_int, [c_void_p, c_void_p, c_int64, c_void_p, c_void_p]),
     "sd_query_noalloc": (ctypes.c_int, [c_void_p, c_void_p, c_int64, c_void_p, c_void_p, c_void_p]),
+    "sd_pose_query": (ctypes.c_int, [c_void_p, c_void_p, c_int64, c_void_p, c_void_p, c_void_p, c_void_p,
+                                     ctypes.POINTER(SdQueryOpts), c_void_p]),
+    "sd_pose_reduce": (ctypes.c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_void_p, c_float,
+                                      c_void_p, c_void_p, c_void_p]),
     "sd_query_status": (ctypes.c_int, [c_void_p, c_void_p]),
     "sd_kernel_launches": (ctypes.c_int64, []),
     "sd_tree_get_info": (ctypes.c_int, [c_void_p, ctypes.POINTER(SdTreeInfo)]),
