@@ -169,6 +169,33 @@ int sd_pose_query(const sd_tree* t, const float* X0, int64_t M, const double* po
 int sd_pose_reduce(const float* X0, const float* value, const float* grad, const float* gamma, int64_t M,
                    const double* pose, float alpha_q, float* out, float* dX0, void* stream);
 
+/*
+ * Batched rigid bodies against one data mesh (the multi-object evaluation
+ * behind Sec. 4.5's simulations): B bodies with uneven vertex counts,
+ * flattened into one vertex list. sd_batch_run places every vertex from a
+ * per-body pose table, orders all of them on one Morton curve, evaluates
+ * them in ONE persistent traversal launch and reduces each body to
+ * (D_b, dD_b/dp (3), dD_b/dtheta (3)) with D_b the outer LogSumExp of
+ * Eq. lse_full2 over the body's vertices (as sd_pose_reduce).
+ *   sd_batch_create: X0 device [M,3] rest vertices of all bodies (kept by
+ *     pointer; must outlive the batch), offsets host int64 [B+1] with
+ *     offsets[0] = 0 and at least one vertex per body. Allocates all the
+ *     batch's device buffers and synchronises the device.
+ *   sd_batch_set_poses: host double [B,6] poses (theta, p); copied to the
+ *     device on `stream` before the call returns.
+ *   sd_batch_run: alpha_q > 0; block = traversal block size (0 default);
+ *     body_out device [B,7]. Enqueues work on `stream` only: no allocation
+ *     and no synchronisation, so it can be captured in a CUDA graph.
+ *   sd_batch_vertex_outputs: device pointers to the batch's placed vertices
+ *     [M,3], d^ [M] and grad d^ [M,3] of the last run.
+ */
+typedef struct sd_batch sd_batch;
+int sd_batch_create(const sd_tree* t, const float* X0, const int64_t* offsets, int32_t nbodies, sd_batch** out);
+int sd_batch_set_poses(sd_batch* b, const double* poses, void* stream);
+int sd_batch_run(sd_batch* b, float alpha_q, int32_t block, float* body_out, void* stream);
+int sd_batch_vertex_outputs(const sd_batch* b, const float** X, const float** value, const float** grad);
+void sd_batch_free(sd_batch* b);
+
 /* Synchronise `stream`, return and clear the tree's device status word. */
 int sd_query_status(const sd_tree* t, void* stream);
 

@@ -71,6 +71,12 @@ SIGNATURES = {
                                      ctypes.POINTER(SdQueryOpts), c_void_p]),
     "sd_pose_reduce": (ctypes.c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_void_p, c_float,
                                       c_void_p, c_void_p, c_void_p]),
+    "sd_batch_create": (ctypes.c_int, [c_void_p, c_void_p, c_void_p, c_int32, ctypes.POINTER(c_void_p)]),
+    "sd_batch_set_poses": (ctypes.c_int, [c_void_p, c_void_p, c_void_p]),
+    "sd_batch_run": (ctypes.c_int, [c_void_p, c_float, c_int32, c_void_p, c_void_p]),
+    "sd_batch_vertex_outputs": (ctypes.c_int, [c_void_p, ctypes.POINTER(c_void_p), ctypes.POINTER(c_void_p),
+                                               ctypes.POINTER(c_void_p)]),
+    "sd_batch_free": (None, [c_void_p]),
     "sd_query_status": (ctypes.c_int, [c_void_p, c_void_p]),
     "sd_kernel_launches": (ctypes.c_int64, []),
     "sd_tree_get_info": (ctypes.c_int, [c_void_p, ctypes.POINTER(SdTreeInfo)]),

@@ -441,3 +441,12 @@ __device__ __forceinline__ void leaf_term(const SdParams& P, float3 q, int k, fl
 void sd_set_last_error(const char* msg);
 int sd_cuda_status(cudaError_t e);
 void sd_count_launches(int k);
+
+// allocation-free pieces of the query path (sd_query.cu), used by the
+// batched multi-body path
+namespace sdint {
+size_t order_scratch_bytes(int m);
+int order_into(const sd_tree* t, const float* q, int m, int32_t* order, void* scratch, cudaStream_t st);
+int traverse(const sd_tree* t, const float* q, int m, const int* order, float* value, float* grad, int block,
+             int* work, cudaStream_t st);
+}

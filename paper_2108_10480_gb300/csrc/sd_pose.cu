@@ -17,6 +17,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <vector>
 
 #include "sd_common.cuh"
 
@@ -236,4 +237,233 @@ extern "C" int sd_pose_reduce(const float* X0, const float* value, const float* 
     e = cudaGetLastError();
     cudaFreeAsync(tmp, st);
     return sd_cuda_status(e);
+}
+
+// ---------------------------------------------------------------------------
+// Batched multi-body evaluation: many rigid bodies with uneven vertex counts
+// against one data mesh. One pass places every body's vertices from a
+// per-body pose table, orders all of them along one Morton curve, runs ONE
+// persistent traversal launch over the flattened list, and reduces each body
+// (outer LogSumExp and 6-DoF gradient). All buffers are allocated when the
+// batch is created; sd_batch_run only enqueues work on the stream (no
+// allocation, no synchronisation), so a caller can capture it in a CUDA
+// graph and replay it.
+// ---------------------------------------------------------------------------
+struct sd_batch {
+    const sd_tree* tree;
+    int B;
+    int M;
+    const float* X0;
+    void* mem;
+    int* body_of;       // [M]
+    float* X;           // [M,3]
+    float* value;       // [M]
+    float* grad;        // [M,3]
+    int32_t* order;     // [M]
+    void* oscratch;     // ordering scratch
+    int* work;          // packet counter
+    PoseF* poses;       // [B]
+    int nchunks;
+    int4* chunks;       // (start, end, body, 0) per chunk, bodies in order
+    int* body_chunk;    // [B + 1] first chunk of each body
+    Part* parts;        // [nchunks]
+    float* fin;         // [B, 9]
+    bool posed;
+};
+
+namespace {
+
+constexpr int CHUNK = 4096;
+
+__global__ void k_batch_place(const float* __restrict__ X0, const int* __restrict__ body_of, int M,
+                              const PoseF* __restrict__ poses, float* __restrict__ X)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= M) return;
+    const PoseF& P = poses[body_of[k]];
+    float3 y = rot(P, f3(X0[3 * k], X0[3 * k + 1], X0[3 * k + 2]));
+    X[3 * k] = y.x + P.p[0];
+    X[3 * k + 1] = y.y + P.p[1];
+    X[3 * k + 2] = y.z + P.p[2];
+}
+
+// one block per chunk of one body: LSE-shifted partial sums
+__global__ void __launch_bounds__(RB) k_batch_partials(const float* __restrict__ X0, const float* __restrict__ value,
+                                                      const float* __restrict__ grad, const int4* __restrict__ chunks,
+                                                      const PoseF* __restrict__ poses, float alpha_q,
+                                                      Part* __restrict__ parts)
+{
+    __shared__ Part sp[RB / 32];
+    const int4 ch = chunks[blockIdx.x];
+    const PoseF& P = poses[ch.z];
+    Part a;
+    a.m = -INFINITY; a.s = 0.f; a.v = 0.f;
+    for (int j = 0; j < 3; ++j) a.gp[j] = a.gt[j] = 0.f;
+    for (int k = ch.x + threadIdx.x; k < ch.y; k += RB) {
+        float d = value[k];
+        float3 g = f3(grad[3 * k], grad[3 * k + 1], grad[3 * k + 2]);
+        float3 y = rot(P, f3(X0[3 * k], X0[3 * k + 1], X0[3 * k + 2]));
+        float3 t = f3(y.y * g.z - y.z * g.y, y.z * g.x - y.x * g.z, y.x * g.y - y.y * g.x);
+        Part b;
+        b.m = -alpha_q * d; b.s = 1.f; b.v = d;
+        b.gp[0] = g.x; b.gp[1] = g.y; b.gp[2] = g.z;
+        b.gt[0] = t.x; b.gt[1] = t.y; b.gt[2] = t.z;
+        part_merge(a, b);
+    }
+    for (int o = 1; o < 32; o <<= 1) {
+        Part b = part_shfl(a, o);
+        part_merge(a, b);
+    }
+    if ((threadIdx.x & 31) == 0) sp[threadIdx.x >> 5] = a;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        Part r = sp[0];
+        for (int w = 1; w < RB / 32; ++w) part_merge(r, sp[w]);
+        parts[blockIdx.x] = r;
+    }
+}
+
+// one thread per body: merge its chunks in order; out[b] = (D, dD/dp, dD/dtheta)
+__global__ void k_batch_final(const Part* __restrict__ parts, const int* __restrict__ body_chunk, int B,
+                              const PoseF* __restrict__ poses, float alpha_q, float* __restrict__ out)
+{
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    Part r = parts[body_chunk[b]];
+    for (int c = body_chunk[b] + 1; c < body_chunk[b + 1]; ++c) part_merge(r, parts[c]);
+    const PoseF& P = poses[b];
+    float n = 1.f / r.s;
+    float gt[3] = {r.gt[0] * n, r.gt[1] * n, r.gt[2] * n};
+    float* o = out + 7 * b;
+    o[0] = -(r.m + logf(r.s)) / alpha_q;
+    for (int j = 0; j < 3; ++j) o[1 + j] = r.gp[j] * n;
+    for (int j = 0; j < 3; ++j) o[4 + j] = P.J[0 * 3 + j] * gt[0] + P.J[1 * 3 + j] * gt[1] + P.J[2 * 3 + j] * gt[2];
+}
+
+__global__ void k_fill_body(int* __restrict__ body_of, int start, int end, int b)
+{
+    int k = start + blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < end) body_of[k] = b;
+}
+
+}  // namespace
+
+extern "C" int sd_batch_create(const sd_tree* t, const float* X0, const int64_t* offsets, int32_t nbodies,
+                               sd_batch** out)
+{
+    if (!out) return SD_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!t || !offsets || nbodies <= 0) return SD_ERR_INVALID_ARG;
+    if (offsets[0] != 0) return SD_ERR_INVALID_ARG;
+    for (int b = 0; b < nbodies; ++b)
+        if (offsets[b + 1] <= offsets[b]) return SD_ERR_INVALID_ARG;   // every body has a vertex
+    int64_t M64 = offsets[nbodies];
+    if (!X0) return SD_ERR_INVALID_ARG;
+    if (M64 >= ((int64_t)1 << 31) / 3) return SD_ERR_TOO_LARGE;
+    const int M = (int)M64, B = nbodies;
+    std::vector<int4> chunks;
+    std::vector<int> body_chunk(B + 1);
+    for (int b = 0; b < B; ++b) {
+        body_chunk[b] = (int)chunks.size();
+        for (int64_t s = offsets[b]; s < offsets[b + 1]; s += CHUNK)
+            chunks.push_back(make_int4((int)s, (int)std::min<int64_t>(s + CHUNK, offsets[b + 1]), b, 0));
+    }
+    body_chunk[B] = (int)chunks.size();
+    const int NC = (int)chunks.size();
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    size_t off = 0;
+    auto carve = [&](size_t bytes) { size_t o = off; off += al(std::max<size_t>(bytes, 1)); return o; };
+    size_t o_body = carve(sizeof(int) * (size_t)M);
+    size_t o_X = carve(sizeof(float) * 3 * (size_t)M);
+    size_t o_v = carve(sizeof(float) * (size_t)M);
+    size_t o_g = carve(sizeof(float) * 3 * (size_t)M);
+    size_t o_ord = carve(sizeof(int32_t) * (size_t)M);
+    size_t o_os = carve(sdint::order_scratch_bytes(M));
+    size_t o_work = carve(sizeof(int));
+    size_t o_pose = carve(sizeof(PoseF) * B);
+    size_t o_ch = carve(sizeof(int4) * NC);
+    size_t o_bc = carve(sizeof(int) * (B + 1));
+    size_t o_parts = carve(sizeof(Part) * NC);
+    size_t o_fin = carve(sizeof(float) * 9 * B);
+    sd_batch* bt = new sd_batch();
+    bt->tree = t; bt->B = B; bt->M = M; bt->X0 = X0; bt->nchunks = NC; bt->posed = false;
+    cudaError_t e = cudaMalloc(&bt->mem, off);
+    if (e != cudaSuccess) { delete bt; cudaGetLastError(); return SD_ERR_OOM; }
+    char* base = (char*)bt->mem;
+    bt->body_of = (int*)(base + o_body);
+    bt->X = (float*)(base + o_X);
+    bt->value = (float*)(base + o_v);
+    bt->grad = (float*)(base + o_g);
+    bt->order = (int32_t*)(base + o_ord);
+    bt->oscratch = base + o_os;
+    bt->work = (int*)(base + o_work);
+    bt->poses = (PoseF*)(base + o_pose);
+    bt->chunks = (int4*)(base + o_ch);
+    bt->body_chunk = (int*)(base + o_bc);
+    bt->parts = (Part*)(base + o_parts);
+    bt->fin = (float*)(base + o_fin);
+    e = cudaMemcpy(bt->chunks, chunks.data(), sizeof(int4) * NC, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(bt->body_chunk, body_chunk.data(), sizeof(int) * (B + 1), cudaMemcpyHostToDevice);
+    for (int b = 0; b < B && e == cudaSuccess; ++b) {
+        int n = (int)(offsets[b + 1] - offsets[b]);
+        k_fill_body<<<(n + 255) / 256, 256>>>(bt->body_of, (int)offsets[b], (int)offsets[b + 1], b);
+        e = cudaGetLastError();
+    }
+    sd_count_launches(B);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) { cudaFree(bt->mem); delete bt; return sd_cuda_status(e); }
+    *out = bt;
+    return SD_OK;
+}
+
+extern "C" int sd_batch_set_poses(sd_batch* bt, const double* poses, void* stream)
+{
+    if (!bt || !poses) return SD_ERR_INVALID_ARG;
+    std::vector<PoseF> P(bt->B);
+    for (int b = 0; b < bt->B; ++b) {
+        for (int j = 0; j < 6; ++j)
+            if (!std::isfinite(poses[6 * b + j])) return SD_ERR_NONFINITE;
+        pose_from_vector(poses + 6 * b, P[b]);
+    }
+    // pageable source: the copy is staged before the call returns
+    cudaError_t e = cudaMemcpyAsync(bt->poses, P.data(), sizeof(PoseF) * bt->B, cudaMemcpyHostToDevice,
+                                    (cudaStream_t)stream);
+    if (e != cudaSuccess) return sd_cuda_status(e);
+    bt->posed = true;
+    return SD_OK;
+}
+
+extern "C" int sd_batch_run(sd_batch* bt, float alpha_q, int32_t block, float* body_out, void* stream)
+{
+    if (!bt || !body_out || !(alpha_q > 0.f) || !bt->posed) return SD_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int M = bt->M;
+    k_batch_place<<<(M + 255) / 256, 256, 0, st>>>(bt->X0, bt->body_of, M, bt->poses, bt->X);
+    sd_count_launches(1);
+    int rc = sdint::order_into(bt->tree, bt->X, M, bt->order, bt->oscratch, st);
+    if (rc != SD_OK) return rc;
+    rc = sdint::traverse(bt->tree, bt->X, M, bt->order, bt->value, bt->grad, block, bt->work, st);
+    if (rc != SD_OK) return rc;
+    k_batch_partials<<<bt->nchunks, RB, 0, st>>>(bt->X0, bt->value, bt->grad, bt->chunks, bt->poses, alpha_q,
+                                                  bt->parts);
+    k_batch_final<<<(bt->B + 63) / 64, 64, 0, st>>>(bt->parts, bt->body_chunk, bt->B, bt->poses, alpha_q,
+                                                     body_out);
+    sd_count_launches(2);
+    return sd_cuda_status(cudaGetLastError());
+}
+
+extern "C" int sd_batch_vertex_outputs(const sd_batch* bt, const float** X, const float** value, const float** grad)
+{
+    if (!bt) return SD_ERR_INVALID_ARG;
+    if (X) *X = bt->X;
+    if (value) *value = bt->value;
+    if (grad) *grad = bt->grad;
+    return SD_OK;
+}
+
+extern "C" void sd_batch_free(sd_batch* bt)
+{
+    if (!bt) return;
+    if (bt->mem) cudaFree(bt->mem);
+    delete bt;
 }

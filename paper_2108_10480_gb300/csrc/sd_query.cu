@@ -654,3 +654,54 @@ extern "C" int sd_query_noalloc(const sd_tree* t, const float* q, int64_t M, flo
     sd_count_launches(nl + 1);
     return sd_cuda_status(cudaGetLastError());
 }
+
+// ---------------------------------------------------------------------------
+// allocation-free building blocks for the batched multi-body path
+// ---------------------------------------------------------------------------
+namespace sdint {
+
+size_t order_scratch_bytes(int m)
+{
+    return sizeof(unsigned) * 2 * (size_t)m + sizeof(int) * (size_t)m + sizeof(uint32_t) * sdsort::hist_words(m) + 256;
+}
+
+// Morton order of m queries into `order`, using caller scratch of
+// order_scratch_bytes(m) bytes (256-byte aligned).
+int order_into(const sd_tree* t, const float* q, int m, int32_t* order, void* scratch, cudaStream_t st)
+{
+    if (m <= 0) return SD_OK;
+    unsigned* k0 = (unsigned*)scratch;
+    unsigned* k1 = k0 + m;
+    int* v1 = (int*)(k1 + m);
+    uint32_t* hist = (uint32_t*)(v1 + m);
+    const sd_tree_info& I = t->info;
+    float3 lo = make_float3(I.scene_lo[0], I.scene_lo[1], I.scene_lo[2]);
+    float ex[3];
+    for (int j = 0; j < 3; ++j) ex[j] = I.scene_hi[j] - I.scene_lo[j];
+    float3 ie = make_float3(ex[0] > 0 ? 1.f / ex[0] : 0.f, ex[1] > 0 ? 1.f / ex[1] : 0.f, ex[2] > 0 ? 1.f / ex[2] : 0.f);
+    int nl = 1;
+    k_query_codes<<<(m + 255) / 256, 256, 0, st>>>(q, m, lo, ie, k0, order);
+    int where = sdsort::sort_pairs<unsigned, int>(k0, order, k1, v1, m, 24, hist, st, &nl);
+    if (where) cudaMemcpyAsync(order, v1, sizeof(int) * (size_t)m, cudaMemcpyDeviceToDevice, st);
+    sd_count_launches(nl);
+    return sd_cuda_status(cudaGetLastError());
+}
+
+// Barnes-Hut traversal with a caller-provided packet counter (zeroed here).
+int traverse(const sd_tree* t, const float* q, int m, const int* order, float* value, float* grad, int block,
+             int* work, cudaStream_t st)
+{
+    if (m <= 0) return SD_OK;
+    if (block < 0 || block > PK_MAX_THREADS || (block % 32) != 0) return SD_ERR_INVALID_ARG;
+    if (t->info.n_prims == 0) {
+        k_fill_empty<<<(m + 255) / 256, 256, 0, st>>>(value, grad, m);
+        sd_count_launches(1);
+        return sd_cuda_status(cudaGetLastError());
+    }
+    cudaMemsetAsync(work, 0, sizeof(int), st);
+    dispatch<false>(t, q, m, order, value, grad, nullptr, block, work, st);
+    sd_count_launches(1);
+    return sd_cuda_status(cudaGetLastError());
+}
+
+}  // namespace sdint
