@@ -53,6 +53,16 @@ SMS, LANES, SM_MAX_GHZ = 152, 128, 2.07
 FP32_PEAK_TFLOPS = SMS * LANES * 2 * SM_MAX_GHZ / 1e3
 
 
+_SCENE = {}
+
+
+def _street():
+    """The street workload, generated once per process."""
+    if "street" not in _SCENE:
+        _SCENE["street"] = synth.config3_scene()
+    return _SCENE["street"]
+
+
 def _args():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
@@ -319,7 +329,7 @@ def _batch_leg(args, dev, reps=10):
     from paper_2108_10480_gb300 import SmoothDistance
     from paper_2108_10480_gb300 import pose as gp
     from paper_2108_10480_gb300.batch import BatchedBodies, autotune
-    s = synth.config3_scene()
+    s = _street()
     bl = synth.config4_bodies()
     bodies = [b["V0"] for b in bl]
     poses = np.array([np.concatenate([b["theta"], b["p"]]) for b in bl])
@@ -375,7 +385,7 @@ def _pose_leg(args, dev, iters=20):
 
     from paper_2108_10480_gb300 import SmoothDistance
     from paper_2108_10480_gb300 import pose as gp
-    s = synth.config3_scene()
+    s = _street()
     b = synth.config3_body()
     P = torch.from_numpy(s["points"]).to(dev)
     Vw = torch.from_numpy(s["wire_V"]).to(dev)
