@@ -44,12 +44,16 @@ M_QUERIES = 262144
 # comparisons/selects not counted): one Barnes-Hut test of a child box, the
 # extra work of an accepted far-field node, and one exact triangle term
 # (closest point, degree-7 weight by de Casteljau and its gradient, LSE
-# update). The derivation is in the design doc.
+# update).
 FLOPS_TEST = 26
 FLOPS_FAR = 26
 FLOPS_TRI = 737
 # FP32 peak: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz maximum SM clock
 SMS, LANES, SM_MAX_GHZ = 152, 128, 2.07
+# tensor-core flops per query of the surrogate network, value and input
+# gradient: forward 80x128 + 2 x 128x128 MACs (layer 1 padded to 80 inputs),
+# backward 2 x 128x128 + 128x80 MACs, 2 flops per MAC
+MLP_FLOPS = 2 * 2 * (80 * 128 + 2 * 128 * 128)
 FP32_PEAK_TFLOPS = SMS * LANES * 2 * SM_MAX_GHZ / 1e3
 
 
@@ -313,7 +317,90 @@ def _extras(args, c, V, F, q, dev, M):
     res["cpu_baseline"] = _cpu_baseline(c, args)
     res["pose"] = _pose_leg(args, dev)
     res["batch"] = _batch_leg(args, dev)
+    res["surrogate"] = _surrogate_leg(args, dev)
     return res
+
+
+def _surrogate_leg(args, dev, reps=3):
+    """Learned far-field surrogate on the street (2,000,000 points + 50,000
+    wire segments, alpha 50, beta 0.5): the network is trained by the
+    library's kernels on Barnes-Hut values of 10M uniform samples of the
+    scene box padded by 5 m (those whose certified bound exceeds 0.5 m), then
+    16M mixed queries (half uniform in the padded box, half within ~1 m of
+    the lidar points) are answered with LB > 1 m routed to LB + the network
+    (trained on the residual over LB) and the rest to the traversal; value +
+    gradient, compared with the traversal alone on the same queries."""
+    import torch
+
+    from paper_2108_10480_gb300 import SmoothDistance
+    from paper_2108_10480_gb300.surrogate import Surrogate, lower_bound
+    s = _street()
+    sd = SmoothDistance(points=s["points"], edges=(s["wire_V"], s["wire_E"]), alpha=50.0, beta=0.5, device=dev)
+    lo = np.minimum(s["points"].min(0), s["wire_V"].min(0)) - 5.0
+    hi = np.maximum(s["points"].max(0), s["wire_V"].max(0)) + 5.0
+    t0 = time.perf_counter()
+    xs = torch.from_numpy(synth.uniform_box(10_000_000, lo, hi, 21)).to(dev)
+    lbs, _, far = lower_bound(sd, xs, margin=0.5, grad=False)
+    xs = xs[far.bool()].contiguous()
+    ts, _ = sd.query(xs, grad=False)
+    sur = Surrogate(lo, hi, sigma=12.0, seed=1, scale=float((ts - lbs[far.bool()]).abs().max()), device=dev)
+    hist = sur.fit_residual(sd, xs, ts, epochs=3, batch=4096, lr=1e-3)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    del xs, ts, lbs
+    n = 16 * 1024 * 1024
+    rng = np.random.default_rng(22)
+    near = s["points"][rng.integers(0, s["points"].shape[0], n // 2)] + \
+        rng.normal(0.0, 0.6, (n // 2, 3)).astype(np.float32)
+    q = torch.from_numpy(np.concatenate([synth.uniform_box(n - n // 2, lo, hi, 23), near])).to(dev)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    vb, gb = torch.empty(n, device=dev), torch.empty(n, 3, device=dev)
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    ms_bh = timed(lambda: sd.query(q, out=(vb, gb)))
+    res = {}
+
+    def routed():
+        res["out"] = sur.query(sd, q, margin=1.0)
+    ms_sur = timed(routed)
+    v, g, r, nr = res["out"]
+    rb = r.bool()
+    qr = q[rb].contiguous()
+    ms_mlp = timed(lambda: sur.forward(qr))
+    ms_lb = timed(lambda: lower_bound(sd, q, margin=1.0))
+    err = (v[rb] - vb[rb]).abs()
+    lbq, _, _ = lower_bound(sd, q, margin=1.0, grad=False)
+    err_lb = (lbq[rb] - vb[rb]).abs()
+    gerr = (g[rb] - gb[rb]).norm(dim=1)
+    return {"what": "street, 16M mixed queries (8M uniform in the box padded by 5 m, 8M near the points); "
+                    "LB > 1 m -> MLP, else Barnes-Hut; value + gradient",
+            "train": {"samples": int(far.sum().item()), "epochs": 3, "batch": 4096, "seconds": train_s,
+                      "loss_first_epoch": hist[0], "loss_last_epoch": hist[-1]},
+            "routed_fraction": nr / n, "ms_routed": ms_sur, "ms_barnes_hut": ms_bh,
+            "speedup": ms_bh / ms_sur, "value": n / (ms_sur / 1e3), "unit": "queries/s",
+            "ms_lower_bound_all": ms_lb,
+            "mlp_forward": {"queries": nr, "ms": ms_mlp, "queries_per_s": nr / (ms_mlp / 1e3),
+                            "tflops": nr * MLP_FLOPS / (ms_mlp / 1e3) / 1e12, "flops_per_query": MLP_FLOPS},
+            "abs_err_m": {"p50": _pct(err, 0.5), "p99": _pct(err, 0.99), "max": float(err.max().item())},
+            "lb_alone_abs_err_m": {"p50": _pct(err_lb, 0.5), "p99": _pct(err_lb, 0.99)},
+            "grad_err": {"p50": _pct(gerr, 0.5), "p99": _pct(gerr, 0.99), "max": float(gerr.max().item())}}
+
+
+def _pct(x, p):
+    if x.numel() == 0:
+        return None
+    xs = x.sort().values
+    return float(xs[int(p * (x.numel() - 1))].item())
 
 
 def _batch_leg(args, dev, reps=10):

@@ -196,6 +196,64 @@ int sd_batch_run(sd_batch* b, float alpha_q, int32_t block, float* body_out, voi
 int sd_batch_vertex_outputs(const sd_batch* b, const float** X, const float** value, const float** grad);
 void sd_batch_free(sd_batch* b);
 
+/*
+ * Learned far-field surrogate (an extension of the method; the paper has none).
+ * A Fourier-feature MLP, parameters in one fp32 vector of
+ * sd_mlp_num_params() floats laid out (B [32,3], W1 [128,67], b1, W2
+ * [128,128], b2, W3 [128,128], b3, w4 [128], b4):
+ *   xh = (x - c)/h per axis, f = [xh, sin(pi B xh), cos(pi B xh)],
+ *   a_l = silu(W_l a_{l-1} + b_l) (l = 1..3), y = s (w4 . a3 + b4),
+ * W_l and w4 used rounded to bfloat16 with fp32 accumulation.
+ * frame = host float[7] = (c_x, c_y, c_z, h_x, h_y, h_z, s): box centre,
+ * half extents (> 0) and output scale; SD_ERR_INVALID_ARG otherwise.
+ *   sd_mlp_forward: device x [n,3] -> y [n] and, if dydx is not NULL,
+ *     dy/dx [n,3] (bf16 tensor-core kernel; input gradient by
+ *     back-propagation).
+ *   sd_mlp_train_step: one mean-squared-error step on a device batch
+ *     (x [n,3], target [n]): writes loss (device [1]) and the gradient
+ *     (device [num_params], zero for B); if lr > 0 also an Adam step (step
+ *     >= 1, moments adam_m/adam_v device [num_params]) on every parameter but
+ *     B. workspace: device, >= sd_mlp_workspace_bytes(n). Deterministic.
+ */
+int64_t sd_mlp_num_params(void);
+size_t sd_mlp_workspace_bytes(int64_t n);
+int sd_mlp_forward(const float* params, const float* frame, const float* x, int64_t n, float* y, float* dydx,
+                   void* stream);
+int sd_mlp_train_step(float* params, float* adam_m, float* adam_v, int32_t step, float lr, const float* frame,
+                      const float* x, const float* target, int64_t n, float* loss, float* grad, void* workspace,
+                      size_t ws_bytes, void* stream);
+
+/*
+ * Certified lower bound of the exact d^ (Eq. 3) from a cut of at most 64
+ * top nodes of the tree (breadth-first from the root while the next level
+ * has at most 64 nodes):
+ *   LB(q) = -(1/alpha) ln sum_{B in cut} n_B w_B kappa^S e^{-alpha d(q, box B)}
+ * with w_B the far-field weight (1 for points-only nodes, max(A_E, A_T)^S
+ * otherwise) and kappa >= 1 a bound of the blending polynomials w~ (their
+ * largest Bernstein coefficient, times 1.0001 for fp32), lowered by
+ * 1e-3 + 1e-5 |LB| for fp32 rounding. It does not bound the Barnes-Hut
+ * value: a far field taken at a node above the cut sits at a nearer box and
+ * can fall below LB (both stay below the exact d^).
+ * Writes device lb [M], lb_grad [M,3] (the gradient of LB before the
+ * rounding allowance: sum_B softmax_B (q - y_B)/|q - y_B|, y_B the closest
+ * point of box B, 0 inside a box) and flag [M] = (LB > margin); any of the
+ * three may be NULL. Uses stream-ordered temporary memory.
+ */
+int sd_lower_bound(const sd_tree* t, const float* q, int64_t M, float margin, float* lb, float* lb_grad,
+                   int32_t* flag, void* stream);
+
+/*
+ * Surrogate-routed query: queries whose certified lower bound exceeds
+ * `margin` are answered by LB plus the MLP (the network models the residual
+ * d^ - LB; value and gradient), all others by the Barnes-Hut traversal, so
+ * the constraint near contact is always the method itself. routed (device
+ * [M], may be NULL) receives 1 for surrogate answers; *n_routed (host, may
+ * be NULL) their count. Synchronises `stream` once (to size the two
+ * groups). Uses stream-ordered temporary memory.
+ */
+int sd_surrogate_query(const sd_tree* t, const float* params, const float* frame, float margin, const float* q,
+                       int64_t M, float* value, float* grad, int32_t* routed, int64_t* n_routed, void* stream);
+
 /* Synchronise `stream`, return and clear the tree's device status word. */
 int sd_query_status(const sd_tree* t, void* stream);
 

@@ -78,6 +78,9 @@ def _load():
         lib.orc_bh.argtypes = [P, d, d, d, i, i, i, P, i64, P, P, P, P, i]
         lib.orc_bh.restype = i
         lib.orc_pose_f32.argtypes = [P, P, P, i64, P]
+        lib.orc_lower_bound.argtypes = [P, d, d, i, P, i64, P, P, P]
+        lib.orc_lower_bound.restype = i
+        lib.orc_prim_kappa.argtypes = [P, P]
         _lib = lib
         return lib
 
@@ -135,6 +138,13 @@ class Scene:
         iso = np.zeros(self.n, np.int32)
         _load().orc_prim_params(self._h, _ptr(out), _ptr(kind), _ptr(iso))
         return out, kind, iso
+
+    def prim_kappa(self):
+        """[n, 4]: largest Bernstein coefficient of each primitive's w~ and
+        its corner coefficients (x = 0, x = 1, y = 1; NaN where absent)."""
+        out = np.zeros((self.n, 4))
+        _load().orc_prim_kappa(self._h, _ptr(out))
+        return out
 
     def prim_eval(self, i, q, alpha=100.0, alpha_u=0.0, paper_metric=False):
         """One primitive at one FP64 query: dict(d, grad_d, phi, wt, grad_wt,
@@ -205,3 +215,17 @@ class Scene:
         if rc != 0:
             raise RuntimeError("orc_bh failed")
         return val, grad, counts, margin
+
+    def lower_bound(self, q, alpha, alpha_u=0.0, unit=False):
+        """Certified lower bound of the exact d^ over the top cut (at most 64
+        nodes) of this scene's tree, its gradient, kappa and the cut size."""
+        if self.L is None:
+            self.build_tree(1)
+        q = np.ascontiguousarray(np.asarray(q, np.float64).reshape(-1, 3))
+        m = q.shape[0]
+        lb = np.zeros(m); grad = np.zeros((m, 3)); info = np.zeros(2)
+        rc = _load().orc_lower_bound(self._h, float(alpha), float(alpha_u), int(bool(unit)), _ptr(q), m, _ptr(lb),
+                                     _ptr(grad), _ptr(info))
+        if rc != 0:
+            raise RuntimeError("orc_lower_bound failed")
+        return lb, grad, float(info[0]), int(info[1])

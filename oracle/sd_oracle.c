@@ -875,6 +875,150 @@ int orc_bh(void *h, double alpha, double alpha_u, double beta, int paper_metric,
 }
 
 /* ------------------------------------------------------------------------ */
+/* certified lower bound of d^ over a top cut of the tree                   */
+/* ------------------------------------------------------------------------ */
+/* Every exact term w_i e^{-alpha d_i} of a primitive inside a node B has
+   d_i >= d(q, box B) and w_i = (A w~_i)^S <= (A kappa)^S when kappa bounds
+   w~ (a Bernstein polynomial lies below its largest coefficient), so
+     LB(q) = -(1/alpha) ln sum_{B in cut} n_B w_B kappa^S e^{-alpha d(q, box B)}
+   with w_B the far-field weight (1 for points-only nodes, max(A_E, A_T)^S
+   otherwise) is below the exact d^ of Eq. 3 for any cut that covers every
+   primitive once. The cut: breadth-first from the root, one level at a
+   time, while the next level has at most 64 nodes (leaves stay). */
+static double binom(int n, int k)
+{
+    double r = 1.0;
+    for (int i = 1; i <= k; ++i) r = r * (double)(n - k + i) / (double)i;
+    return r;
+}
+
+/* largest Bernstein coefficient of w~ on one primitive, by the change of
+   basis from the monomial form the weights are stored in:
+   degree n in x:  beta_i = sum_{k<=i} C(i,k) / C(n,k) c_k;
+   degree n on the triangle (1-x-y, x, y):
+     beta_{.jk} = sum_{a<=j, b<=k} C(j,a) C(k,b) a! b! (n-a-b)! / n! c_{ab} */
+static double prim_kappa(const scene_t *s, const prim_t *p, double *corner)
+{
+    corner[0] = corner[1] = corner[2] = 1.0;
+    if (p->kind == K_SEG) {
+        double c[5], best = -INFINITY;
+        for (int k = 0; k < 5; ++k) c[k] = s->ebasis[k][0] * p->pa + s->ebasis[k][1] * p->pb + s->ebasis[k][2];
+        for (int i = 0; i <= 4; ++i) {
+            double b = 0.0;
+            for (int k = 0; k <= i; ++k) b += binom(i, k) / binom(4, k) * c[k];
+            if (b > best) best = b;
+            if (i == 0) corner[0] = b;
+            if (i == 4) corner[1] = b;
+        }
+        corner[2] = NAN;
+        return best;
+    }
+    if (p->kind == K_TRI) {
+        if (p->isolated) return 1.0;
+        double c[8][8];
+        memset(c, 0, sizeof(c));
+        double rhs[3] = {p->pa, p->pb, 1.0 - p->pa};
+        for (int j = 0; j < 36; ++j)
+            c[s->texp[j][0]][s->texp[j][1]] +=
+                s->tbasis[j][0] * rhs[0] + s->tbasis[j][1] * rhs[1] + s->tbasis[j][2] * rhs[2];
+        double best = -INFINITY;
+        for (int j = 0; j <= 7; ++j)
+            for (int k = 0; j + k <= 7; ++k) {
+                double b = 0.0;
+                for (int a = 0; a <= j; ++a)
+                    for (int bb = 0; bb <= k; ++bb)
+                        b += binom(j, a) * binom(k, bb) / (binom(7, a) * binom(7 - a, bb)) * c[a][bb];
+                if (b > best) best = b;
+                if (j == 0 && k == 0) corner[0] = b;
+                if (j == 7) corner[1] = b;
+                if (k == 7) corner[2] = b;
+            }
+        return best;
+    }
+    return 1.0;
+}
+
+/* per primitive: largest Bernstein coefficient of w~ and the coefficients at
+   the corners (x = 0, x = 1 [, y = 1]); out [n, 4] */
+void orc_prim_kappa(void *h, double *out)
+{
+    scene_t *s = (scene_t *)h;
+    for (int64_t i = 0; i < s->n; ++i) out[4 * i] = prim_kappa(s, &s->P[i], out + 4 * i + 1);
+}
+
+/* out: kappa, cut size. lb [m], grad [m,3] (grad may be NULL). */
+int orc_lower_bound(void *h, double alpha, double alpha_u, int unit, const double *q, int64_t m, double *lb,
+                    double *grad, double *info)
+{
+    scene_t *s = (scene_t *)h;
+    if (s->n == 0 || s->nb == 0) return -1;
+    double S = alpha / (alpha > alpha_u ? alpha : alpha_u);
+    double kappa = 1.0;
+    if (!unit)
+        for (int64_t i = 0; i < s->n; ++i) {
+            double corner[3];
+            double k = prim_kappa(s, &s->P[i], corner);
+            if (k > kappa) kappa = k;
+        }
+    double A = s->A_E > s->A_T ? s->A_E : s->A_T;
+    double wfar = unit ? 1.0 : pow(A, S);
+    enum { CUT = 64 };
+    int32_t cur[CUT], nxt[CUT];  /* >= 0 internal node, < 0 leaf -(b+1) */
+    int n = 1;
+    cur[0] = s->nb > 1 ? 0 : -1;
+    for (;;) {
+        int nn = 0;
+        for (int i = 0; i < n; ++i) nn += cur[i] >= 0 ? 2 : 1;
+        if (nn > CUT || nn == n) break;
+        int o = 0;
+        for (int i = 0; i < n; ++i) {
+            if (cur[i] < 0) nxt[o++] = cur[i];
+            else { nxt[o++] = s->left[cur[i]]; nxt[o++] = s->right[cur[i]]; }
+        }
+        memcpy(cur, nxt, sizeof(int32_t) * o);
+        n = o;
+    }
+    double lw[CUT];
+    const float *lo[CUT], *hi[CUT];
+    for (int i = 0; i < n; ++i) {
+        int64_t cnt; int po;
+        if (cur[i] < 0) {
+            int64_t b = -(int64_t)cur[i] - 1;
+            lo[i] = s->llo[b]; hi[i] = s->lhi[b]; cnt = s->lcount[b]; po = s->lpts_only[b];
+        } else {
+            lo[i] = s->nlo[cur[i]]; hi[i] = s->nhi[cur[i]]; cnt = s->ncount[cur[i]]; po = s->npts_only[cur[i]];
+        }
+        lw[i] = log((double)cnt * (po ? 1.0 : wfar)) + S * log(kappa);
+    }
+    for (int64_t k = 0; k < m; ++k) {
+        const double *x = q + 3 * k;
+        double t[CUT], dv[CUT][3], d[CUT], mx = -INFINITY;
+        for (int i = 0; i < n; ++i) {
+            for (int j = 0; j < 3; ++j) {
+                double l = lo[i][j], u = hi[i][j];
+                double y = x[j] < l ? l : (x[j] > u ? u : x[j]);
+                dv[i][j] = x[j] - y;
+            }
+            d[i] = sqrt(dot3(dv[i], dv[i]));
+            t[i] = lw[i] - alpha * d[i];
+            if (t[i] > mx) mx = t[i];
+        }
+        double sum = 0.0, g[3] = {0, 0, 0};
+        for (int i = 0; i < n; ++i) {
+            double e = exp(t[i] - mx);
+            sum += e;
+            if (d[i] > 0.0)
+                for (int j = 0; j < 3; ++j) g[j] += e * dv[i][j] / d[i];
+        }
+        lb[k] = -(mx + log(sum)) / alpha;
+        if (grad)
+            for (int j = 0; j < 3; ++j) grad[3 * k + j] = g[j] / sum;
+    }
+    if (info) { info[0] = kappa; info[1] = (double)n; }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
 /* rigid placement of query vertices in fp32                                */
 /* ------------------------------------------------------------------------ */
 /* x_k = R x0_k + p evaluated in fp32 in the fixed order

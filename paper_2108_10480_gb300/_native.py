@@ -77,6 +77,15 @@ SIGNATURES = {
     "sd_batch_vertex_outputs": (ctypes.c_int, [c_void_p, ctypes.POINTER(c_void_p), ctypes.POINTER(c_void_p),
                                                ctypes.POINTER(c_void_p)]),
     "sd_batch_free": (None, [c_void_p]),
+    "sd_mlp_num_params": (ctypes.c_int64, []),
+    "sd_mlp_workspace_bytes": (ctypes.c_size_t, [c_int64]),
+    "sd_mlp_forward": (ctypes.c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_void_p, c_void_p, c_void_p]),
+    "sd_mlp_train_step": (ctypes.c_int, [c_void_p, c_void_p, c_void_p, c_int32, c_float, c_void_p, c_void_p,
+                                         c_void_p, c_int64, c_void_p, c_void_p, c_void_p, ctypes.c_size_t,
+                                         c_void_p]),
+    "sd_lower_bound": (ctypes.c_int, [c_void_p, c_void_p, c_int64, c_float, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "sd_surrogate_query": (ctypes.c_int, [c_void_p, c_void_p, c_void_p, c_float, c_void_p, c_int64, c_void_p,
+                                          c_void_p, c_void_p, ctypes.POINTER(c_int64), c_void_p]),
     "sd_query_status": (ctypes.c_int, [c_void_p, c_void_p]),
     "sd_kernel_launches": (ctypes.c_int64, []),
     "sd_tree_get_info": (ctypes.c_int, [c_void_p, ctypes.POINTER(SdTreeInfo)]),
