@@ -68,6 +68,10 @@ def _street():
 
 
 def _args():
+    return _args_from(None)
+
+
+def _args_from(argv):
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
     p.add_argument("--steps", type=int, default=100)
@@ -78,7 +82,7 @@ def _args():
     p.add_argument("--leaf-size", type=int, default=LEAF)
     p.add_argument("--queries", type=int, default=M_QUERIES)
     p.add_argument("--no-extras", action="store_true", help="skip plain/e2e/cpu baseline legs")
-    return p.parse_args()
+    return p.parse_args(argv)
 
 
 def _workload(args, rank=0):
@@ -161,6 +165,23 @@ class _Clocks:
                 "reasons": sorted(reasons)}
 
 
+def _max_over_ranks(ms, device):
+    """The slowest rank's time per step; every rank calls it (a no-op
+    without a process group)."""
+    import torch
+    import torch.distributed as dist
+    if not dist.is_initialized() or dist.get_world_size() == 1:
+        return ms
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _job_value(ms, per_rank_units, world):
+    """Whole-job throughput: every rank's units over the slowest rank's time."""
+    return world * per_rank_units / (ms / 1e3)
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -224,12 +245,8 @@ def run_ours(args):
     step_ms = [e[0].elapsed_time(e[2]) for e in evs]
     trav_ms = [e[1].elapsed_time(e[2]) for e in evs]
     build_ms = [e[0].elapsed_time(e[1]) for e in evs]
-    ms = sum(step_ms) / len(step_ms)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * M / (ms / 1e3)
+    ms = _max_over_ranks(sum(step_ms) / len(step_ms), dev)
+    value = _job_value(ms, M, world)
 
     out = None
     if rank == 0:
@@ -551,7 +568,7 @@ def run_reference(args):
     return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded generators, synth/)",
-            "config": _config(args, 1), "impl": "reference",
+            "config": _config(args, args.gpus), "impl": "reference",
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"per step: oracle tree build + Barnes-Hut on {sample} of {M} queries, "
                                        f"scaled to the full batch"},
