@@ -331,7 +331,7 @@ def _extras(args, c, V, F, q, dev, M):
     res["e2e"] = {"value": M / (te / 1e3), "unit": UNIT, "ms_per_step": te,
                   "h2d_bytes_per_step": int(hV.numel() * 4 + hF.numel() * 4 + hq.numel() * 4),
                   "d2h_bytes_per_step": int(hv.numel() * 4 + hg.numel() * 4)}
-    res["cpu_baseline"] = _cpu_baseline(c, args)
+    res["cpu_baseline"] = _cpu_baseline(c, args, min_seconds=10.0)
     res["pose"] = _pose_leg(args, dev)
     res["batch"] = _batch_leg(args, dev)
     res["surrogate"] = _surrogate_leg(args, dev)
@@ -524,27 +524,37 @@ def _pose_leg(args, dev, iters=20):
             "D": float(out[0].item())}
 
 
-def _cpu_baseline(c, args, sample=None):
+def _cpu_baseline(c, args, sample=None, min_seconds=0.0):
     """The FP64 oracle as it stands on this host's cores: its own tree build
-    over the full mesh plus Barnes-Hut on a query sample; the rate is scaled
-    to the full batch as M / (t_build + t_query * M / sample)."""
+    over the full mesh plus Barnes-Hut on a query sample (repeated until
+    min_seconds of work); the rate is scaled to the full batch as
+    M / (t_build + t_query * M / sample)."""
     import oracle
     cores = oracle.default_threads()
     M = c["queries"].shape[0]
     if sample is None:
-        sample = min(M, 8192 * max(1, cores // 2))
+        sample = M
     qs = c["queries"][:sample]
-    t0 = time.perf_counter()
-    sc = oracle.Scene(tri_V=c["V"], tri_F=c["F"])
-    sc.build_tree(args.leaf_size)
-    t1 = time.perf_counter()
-    sc.bh(qs, args.alpha, args.beta, threads=cores)
-    t2 = time.perf_counter()
-    tb, tq = t1 - t0, t2 - t1
+    tb = tq = 0.0
+    reps = 0
+    t_start = time.perf_counter()
+    while reps == 0 or time.perf_counter() - t_start < min_seconds:
+        t0 = time.perf_counter()
+        sc = oracle.Scene(tri_V=c["V"], tri_F=c["F"])
+        sc.build_tree(args.leaf_size)
+        t1 = time.perf_counter()
+        sc.bh(qs, args.alpha, args.beta, threads=cores)
+        t2 = time.perf_counter()
+        tb += t1 - t0
+        tq += t2 - t1
+        reps += 1
+    tb /= reps
+    tq /= reps
     full = tb + tq * M / sample
     return {"value": M / full, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"oracle tree build over all 81,920 triangles ({tb:.2f} s) + FP64 Barnes-Hut on the first "
-                      f"{sample} of {M} queries ({tq:.2f} s, {cores} threads); rate scaled to the full batch"}
+            "sample": f"{reps} x (oracle tree build over all 81,920 triangles ({tb:.2f} s) + FP64 Barnes-Hut on "
+                      f"{'all' if sample == M else f'the first {sample} of'} {M} queries ({tq:.2f} s, {cores} "
+                      f"threads)); mean per pass" + ("" if sample == M else ", rate scaled to the full batch")}
 
 
 def run_reference(args):
