@@ -55,6 +55,9 @@ typedef struct {
     int32_t weights;      /* SD_WEIGHTS_PAPER: w_i = (A w~_i)^S of App. C; SD_WEIGHTS_UNIT: w_i = 1 */
     int32_t paper_metric; /* 1: barycentric gradients measured in the alpha-scaled metric of Sec. 3.3
                              (the weight-gradient term is divided by alpha once more); 0: exact gradient */
+    int32_t defer_checks; /* 0 (default): sd_build waits for the device and returns data errors itself;
+                             1: sd_build only enqueues work and returns SD_OK; data errors are reported
+                             by sd_query_status, and sd_tree_get_info waits for the build */
 } sd_build_opts;
 
 typedef struct {
@@ -87,8 +90,11 @@ void sd_default_query_opts(sd_query_opts* o);
  *   opts   host pointer or NULL for defaults
  *   out    receives the new tree; the tree owns copies of everything it
  *          needs, so `g`'s arrays may be freed after the call returns.
- * Synchronises `stream` before returning (it reports data errors such as
- * SD_ERR_NONFINITE / SD_ERR_INDEX, in which case *out is NULL).
+ * By default synchronises `stream` before returning (it reports data errors
+ * such as SD_ERR_NONFINITE / SD_ERR_INDEX, in which case *out is NULL). With
+ * opts->defer_checks = 1 it returns after enqueueing the build: the same
+ * kernels run (indices are clamped where they are dereferenced, so bad input
+ * cannot fault) and their verdict is reported by sd_query_status.
  */
 int sd_build(const sd_geometry* g, float alpha, float beta, const sd_build_opts* opts,
              void* stream, sd_tree** out);

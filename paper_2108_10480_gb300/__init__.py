@@ -67,7 +67,10 @@ class SmoothDistance:
     and/or a triangle mesh) for fixed alpha and beta (sd_build)."""
 
     def __init__(self, points=None, edges=None, tris=None, alpha=100.0, beta=0.5, alpha_u=0.0,
-                 leaf_size=1, weights="paper", paper_metric=False, device=None, stream=None):
+                 leaf_size=1, weights="paper", paper_metric=False, device=None, stream=None, check=True):
+        """check=True: the build waits for the device and raises on invalid
+        input; check=False: it only enqueues the work (same kernels) and
+        invalid input is reported by status()."""
         L = lib()
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         with torch.cuda.device(self.device):
@@ -87,6 +90,7 @@ class SmoothDistance:
             o.leaf_size = int(leaf_size)
             o.weights = 1 if weights == "unit" else 0
             o.paper_metric = 1 if paper_metric else 0
+            o.defer_checks = 0 if check else 1
             h = ctypes.c_void_p()
             rc = L.sd_build(ctypes.byref(g), float(alpha), float(beta), ctypes.byref(o), _stream_handle(stream),
                             ctypes.byref(h))

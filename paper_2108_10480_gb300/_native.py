@@ -34,7 +34,8 @@ class SdGeometry(ctypes.Structure):
 
 
 class SdBuildOpts(ctypes.Structure):
-    _fields_ = [("alpha_u", c_float), ("leaf_size", c_int32), ("weights", c_int32), ("paper_metric", c_int32)]
+    _fields_ = [("alpha_u", c_float), ("leaf_size", c_int32), ("weights", c_int32), ("paper_metric", c_int32),
+                ("defer_checks", c_int32)]
 
 
 class SdQueryOpts(ctypes.Structure):

@@ -37,6 +37,7 @@ extern "C" void sd_default_build_opts(sd_build_opts* o)
     o->leaf_size = 1;
     o->weights = SD_WEIGHTS_PAPER;
     o->paper_metric = 0;
+    o->defer_checks = 0;
 }
 
 extern "C" void sd_default_query_opts(sd_query_opts* o)

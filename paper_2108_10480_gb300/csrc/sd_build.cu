@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <mutex>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -67,7 +68,7 @@ __device__ __forceinline__ float3 prim_vertex(const Geo& g, int i, int j)
 __device__ __forceinline__ int prim_nv(const Geo& g, int i) { return i < g.np ? 1 : (i < g.np + g.ne ? 2 : 3); }
 
 // --- validation and scene box --------------------------------------------
-__global__ void k_vertices(const float* __restrict__ x, int nv, BuildScalars* bs)
+__device__ __forceinline__ void check_vertices(const float* __restrict__ x, int nv, BuildScalars* bs)
 {
     float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
     bool bad = false;
@@ -96,12 +97,59 @@ __global__ void k_vertices(const float* __restrict__ x, int nv, BuildScalars* bs
     }
 }
 
-__global__ void k_check_index(const int* __restrict__ idx, int64_t count, int nv, BuildScalars* bs)
+__device__ __forceinline__ void check_index(const int* __restrict__ idx, int64_t count, int nv, BuildScalars* bs)
 {
+    bool bad = false;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
         int v = idx[i];
-        if (v < 0 || v >= nv) atomicOr(&bs->status, ST_INDEX);
+        bad |= v < 0 || v >= nv;
     }
+    if (bad) atomicOr(&bs->status, ST_INDEX);
+}
+
+// every input check in one launch: blockIdx.y picks the array (points,
+// edge-mesh vertices, triangle-mesh vertices, edge indices, triangle indices)
+__global__ void k_validate(Geo g, BuildScalars* bs)
+{
+    switch (blockIdx.y) {
+    case 0: check_vertices(g.P, g.np, bs); break;
+    case 1: check_vertices(g.EV, g.nev, bs); break;
+    case 2: check_vertices(g.TV, g.ntv, bs); break;
+    case 3: check_index(g.E, 2 * (int64_t)g.ne, g.nev, bs); break;
+    default: check_index(g.F, 3 * (int64_t)g.nf, g.ntv, bs); break;
+    }
+}
+
+// zero / fill the build's working arrays and its scalars in one launch
+struct InitJob {
+    BuildScalars* bs;
+    int* status;
+    float* params; int nparams;
+    int4* nodes; int nnodes4;
+    int* visits; int nvisits;
+    int* ecnt; int nev;
+    int* vcnt; int ntv;
+    int* hcnt; unsigned long long* hkeys; int hcap;
+};
+
+__global__ void k_init(InitJob J)
+{
+    const int t0 = blockIdx.x * blockDim.x + threadIdx.x, st = gridDim.x * blockDim.x;
+    if (t0 == 0) {
+        BuildScalars b;
+        for (int j = 0; j < 3; ++j) { b.box[j] = 0xffffffffu; b.box[3 + j] = 0u; }
+        b.status = 0;
+        b.A_E = 1; b.A_T = 1;
+        b.pad = 0;
+        *J.bs = b;
+        for (int j = 0; j < 4; ++j) J.status[j] = 0;
+    }
+    for (int i = t0; i < J.nparams; i += st) J.params[i] = 0.f;
+    for (int i = t0; i < J.nnodes4; i += st) J.nodes[i] = make_int4(0, 0, 0, 0);
+    for (int i = t0; i < J.nvisits; i += st) J.visits[i] = 0;
+    for (int i = t0; i < J.nev; i += st) J.ecnt[i] = 0;
+    for (int i = t0; i < J.ntv; i += st) J.vcnt[i] = 0;
+    for (int i = t0; i < J.hcap; i += st) { J.hcnt[i] = 0; J.hkeys[i] = ~0ull; }
 }
 
 // --- incidence counts (App. C.2, C.3): one count per incidence slot -------
@@ -373,13 +421,34 @@ __global__ void k_super_root(SdNode* nodes, float2* nw2, int nb)
     nw2[nb - 1].y = 0.f;
 }
 
+// the tree's scalars from the build's atomics (one thread): weight scales,
+// scene box for query codes, and the validation bits folded into the
+// tree's status word
+__global__ void k_finalize(const BuildScalars* bs, int n, int unit, SdScalars* sc, int* status)
+{
+    if (threadIdx.x || blockIdx.x) return;
+    sc->A_E = unit ? 1.f : (float)bs->A_E;
+    sc->A_T = unit ? 1.f : (float)bs->A_T;
+    for (int j = 0; j < 3; ++j) {
+        float lo = n ? key2f(bs->box[j]) : 0.f, hi = n ? key2f(bs->box[3 + j]) : 0.f;
+        float ex = hi - lo;
+        sc->lo[j] = lo;
+        sc->hi[j] = hi;
+        sc->inv_ex[j] = ex > 0.f ? 1.f / ex : 0.f;
+    }
+    sc->status = bs->status;
+    if (bs->status & ST_INDEX) atomicOr(status, 1 << SD_ERR_INDEX);
+    if (bs->status & ST_NONFINITE) atomicOr(status, 1 << SD_ERR_NONFINITE);
+}
+
 // primitives in leaf order
 __global__ void k_gather(Geo g, const int* __restrict__ sorted, const float* __restrict__ params,
-                         float4* __restrict__ hdr, float4* __restrict__ ext)
+                         float4* __restrict__ hdr, float4* __restrict__ ext, int* __restrict__ sorted_out)
 {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= g.n) return;
     int p = sorted[k];
+    sorted_out[k] = p;
     float3 a = prim_vertex(g, p, 0);
     if (p < g.np) {
         hdr[k] = make_float4(a.x, a.y, a.z, (float)SD_KIND_POINT);
@@ -417,6 +486,52 @@ int load_weight_basis(SdParams& P)
 size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
 }  // namespace
+
+static std::mutex g_use_mu;
+
+void sd_mark_use(const sd_tree* tc, cudaStream_t st)
+{
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) { cudaGetLastError(); return; }
+    if (cs != cudaStreamCaptureStatusNone) return;
+    sd_tree* t = const_cast<sd_tree*>(tc);
+    std::lock_guard<std::mutex> g(g_use_mu);
+    int i = 0;
+    while (i < t->n_use && t->use_stream[i] != st) ++i;
+    if (i == t->n_use) {
+        if (t->n_use < 4) {
+            if (cudaEventCreateWithFlags(&t->use_event[i], cudaEventDisableTiming) != cudaSuccess) {
+                // no event: wait for the work now instead
+                cudaGetLastError();
+                cudaStreamSynchronize(st);
+                return;
+            }
+            ++t->n_use;
+        } else {
+            // reuse the oldest slot once its stream's recorded work is done
+            i = t->use_next;
+            t->use_next = (t->use_next + 1) % 4;
+            cudaEventSynchronize(t->use_event[i]);
+        }
+        t->use_stream[i] = st;
+    }
+    cudaEventRecord(t->use_event[i], st);
+}
+
+// the tree info fields that come from the device
+static void fill_info(sd_tree* t, const SdScalars& hs)
+{
+    sd_tree_info& inf = t->info;
+    inf.A_E = hs.A_E;
+    inf.A_T = hs.A_T;
+    float A = std::max(inf.A_E, inf.A_T);
+    inf.w_far = t->weights_unit ? 1.f : (inf.S == 1.f ? A : std::pow(A, inf.S));
+    for (int j = 0; j < 3; ++j) {
+        inf.scene_lo[j] = hs.lo[j];
+        inf.scene_hi[j] = hs.hi[j];
+    }
+    t->info_ready = true;
+}
 
 extern "C" int sd_build(const sd_geometry* g, float alpha, float beta, const sd_build_opts* opts_in,
                         void* stream, sd_tree** out)
@@ -475,6 +590,7 @@ extern "C" int sd_build(const sd_geometry* g, float alpha, float beta, const sd_
     size_t o_lcnt = carve(sizeof(int) * std::max(nb, 1));
     size_t o_params = carve(sizeof(float) * 2 * std::max(n, 1));
     size_t o_status = carve(sizeof(int) * 4);
+    size_t o_sc = carve(sizeof(SdScalars));
     t->mem_bytes = off;
     cudaError_t ce = cudaMallocAsync(&t->mem, off, st);
     if (ce != cudaSuccess) { delete t; cudaGetLastError(); return SD_ERR_OOM; }
@@ -493,6 +609,7 @@ extern "C" int sd_build(const sd_geometry* g, float alpha, float beta, const sd_
     t->leaf_count = (int32_t*)(base + o_lcnt);
     t->params = (float*)(base + o_params);
     t->status = (int*)(base + o_status);
+    t->sc = (SdScalars*)(base + o_sc);
 
     // temporary memory
     size_t toff = 0;
@@ -516,7 +633,7 @@ extern "C" int sd_build(const sd_geometry* g, float alpha, float beta, const sd_
     size_t t_lpts = tcarve(sizeof(int) * std::max(nb, 1));
     void* tmp = nullptr;
     ce = cudaMallocAsync(&tmp, toff, st);
-    if (ce != cudaSuccess) { cudaFree(t->mem); delete t; cudaGetLastError(); return SD_ERR_OOM; }
+    if (ce != cudaSuccess) { cudaFreeAsync(t->mem, st); delete t; cudaGetLastError(); return SD_ERR_OOM; }
     char* tb = (char*)tmp;
     BuildScalars* bs = (BuildScalars*)(tb + t_bs);
     auto* k0 = (unsigned long long*)(tb + t_k0);
@@ -534,39 +651,38 @@ extern "C" int sd_build(const sd_geometry* g, float alpha, float beta, const sd_
     int* npts = (int*)(tb + t_npts);
     int* lpts = (int*)(tb + t_lpts);
 
-    BuildScalars init;
-    std::memset(&init, 0, sizeof(init));
-    for (int j = 0; j < 3; ++j) { init.box[j] = 0xffffffffu; init.box[3 + j] = 0u; }
-    init.A_E = 1; init.A_T = 1;
-    cudaMemcpyAsync(bs, &init, sizeof(init), cudaMemcpyHostToDevice, st);
-    cudaMemsetAsync(t->status, 0, sizeof(int) * 4, st);
-    cudaMemsetAsync(t->params, 0, sizeof(float) * 2 * std::max(n, 1), st);
-    cudaMemsetAsync(t->nodes, 0, sizeof(SdNode) * std::max(nb, 1), st);
-    cudaMemsetAsync(visits, 0, sizeof(int) * std::max(nb, 1), st);
-
     const int T = 256;
     int nl = 0;   // kernel launches of this build
+    {
+        InitJob J;
+        J.bs = bs; J.status = t->status;
+        J.params = t->params; J.nparams = 2 * std::max(n, 1);
+        J.nodes = (int4*)t->nodes; J.nnodes4 = 4 * std::max(nb, 1);
+        J.visits = visits; J.nvisits = std::max(nb, 1);
+        J.ecnt = ecnt; J.nev = geo.ne ? geo.nev : 0;
+        J.vcnt = vcnt; J.ntv = geo.nf ? geo.ntv : 0;
+        J.hcnt = hcnt; J.hkeys = hkeys; J.hcap = geo.nf ? (int)hcap : 0;
+        int work = std::max({J.nparams, J.nnodes4, J.nvisits, J.nev, J.ntv, J.hcap});
+        ++nl;
+        k_init<<<std::min(nblk(work, T), 1024), T, 0, st>>>(J);
+    }
     // validation + scene box over every vertex
-    if (geo.np) { ++nl; k_vertices<<<std::min(nblk(geo.np, T), 1024), T, 0, st>>>(geo.P, geo.np, bs); }
-    if (geo.nev) { ++nl; k_vertices<<<std::min(nblk(geo.nev, T), 1024), T, 0, st>>>(geo.EV, geo.nev, bs); }
-    if (geo.ntv) { ++nl; k_vertices<<<std::min(nblk(geo.ntv, T), 1024), T, 0, st>>>(geo.TV, geo.ntv, bs); }
-    if (geo.ne) { ++nl; k_check_index<<<std::min(nblk(2 * (int64_t)geo.ne, T), 1024), T, 0, st>>>(geo.E, 2 * (int64_t)geo.ne, geo.nev, bs); }
-    if (geo.nf) { ++nl; k_check_index<<<std::min(nblk(3 * (int64_t)geo.nf, T), 1024), T, 0, st>>>(geo.F, 3 * (int64_t)geo.nf, geo.ntv, bs); }
+    {
+        int64_t most = std::max<int64_t>({geo.np, geo.nev, geo.ntv, 2 * (int64_t)geo.ne, 3 * (int64_t)geo.nf, 1});
+        ++nl;
+        k_validate<<<dim3(std::min(nblk(most, T), 1024), 5), T, 0, st>>>(geo, bs);
+    }
     // validation results are read once, at the end of the build; the kernels
     // below clamp every index they dereference
 
     // incidence counts and weight parameters
     if (geo.ne) {
-        cudaMemsetAsync(ecnt, 0, sizeof(int) * geo.nev, st);
         ++nl;
         k_count_slots<<<std::min(nblk(2 * (int64_t)geo.ne, T), 4096), T, 0, st>>>(geo.E, 2 * (int64_t)geo.ne, geo.nev, ecnt);
         ++nl;
         k_edge_params<<<nblk(geo.ne, T), T, 0, st>>>(geo.E, geo.ne, geo.nev, ecnt, t->params, geo.np, bs);
     }
     if (geo.nf) {
-        cudaMemsetAsync(vcnt, 0, sizeof(int) * geo.ntv, st);
-        cudaMemsetAsync(hkeys, 0xff, sizeof(unsigned long long) * hcap, st);
-        cudaMemsetAsync(hcnt, 0, sizeof(int) * hcap, st);
         ++nl;
         k_count_slots<<<std::min(nblk(3 * (int64_t)geo.nf, T), 4096), T, 0, st>>>(geo.F, 3 * (int64_t)geo.nf, geo.ntv, vcnt);
         ++nl;
@@ -582,7 +698,6 @@ extern "C" int sd_build(const sd_geometry* g, float alpha, float beta, const sd_
         int where = sdsort::sort_pairs<unsigned long long, int>(k0, v0, k1, v1, n, 64, hist, st, &nl);
         unsigned long long* sk = where ? k1 : k0;
         int* sv = where ? v1 : v0;
-        cudaMemcpyAsync(t->sorted, sv, sizeof(int) * n, cudaMemcpyDeviceToDevice, st);
         // topology
         if (nb > 1) {
             ++nl;
@@ -596,41 +711,57 @@ extern "C" int sd_build(const sd_geometry* g, float alpha, float beta, const sd_
                                                 npts, t->leaf_box, t->leaf_count, lpts, visits, t->nodes, t->nw2,
                                                 bs, S, t->weights_unit);
         ++nl;
-        k_gather<<<nblk(n, T), T, 0, st>>>(geo, sv, t->params, t->hdr, t->ext);
+        k_gather<<<nblk(n, T), T, 0, st>>>(geo, sv, t->params, t->hdr, t->ext, t->sorted);
     }
-    BuildScalars hb;
-    cudaMemcpyAsync(&hb, bs, sizeof(hb), cudaMemcpyDeviceToHost, st);
+    ++nl;
+    k_finalize<<<1, 32, 0, st>>>(bs, n, t->weights_unit, t->sc, t->status);
     cudaFreeAsync(tmp, st);
     sd_count_launches(nl);
-    ce = cudaStreamSynchronize(st);
-    if (ce == cudaSuccess) ce = cudaGetLastError();
-    int status = SD_OK;
-    if (ce != cudaSuccess) status = sd_cuda_status(ce);
-    else if (hb.status & ST_INDEX) status = SD_ERR_INDEX;
-    else if (hb.status & ST_NONFINITE) status = SD_ERR_NONFINITE;
-    if (status != SD_OK) {
-        cudaFree(t->mem);
-        delete t;
-        return status;
-    }
 
     sd_tree_info& inf = t->info;
     inf.n_prims = n; inf.n_points = geo.np; inf.n_edges = geo.ne; inf.n_tris = geo.nf;
     inf.n_buckets = nb; inf.leaf_size = L;
     inf.alpha = alpha; inf.beta = beta; inf.alpha_u = opts.alpha_u; inf.S = S;
-    inf.A_E = t->weights_unit ? 1.f : (float)hb.A_E;
-    inf.A_T = t->weights_unit ? 1.f : (float)hb.A_T;
-    float A = std::max(inf.A_E, inf.A_T);
-    inf.w_far = t->weights_unit ? 1.f : (S == 1.f ? A : std::pow(A, S));
-    for (int j = 0; j < 3; ++j) {
-        inf.scene_lo[j] = n ? key2f(hb.box[j]) : 0.f;
-        inf.scene_hi[j] = n ? key2f(hb.box[3 + j]) : 0.f;
-    }
     inf.device_bytes = (int64_t)t->mem_bytes;
+    if (opts.defer_checks) {
+        // return at once: the checks' outcome reaches the status word
+        // (sd_query_status), the device scalars reach info on demand
+        ce = cudaEventCreateWithFlags(&t->built, cudaEventDisableTiming);
+        if (ce == cudaSuccess) ce = cudaEventRecord(t->built, st);
+        if (ce == cudaSuccess) ce = cudaGetLastError();
+        if (ce != cudaSuccess) {
+            cudaStreamSynchronize(st);
+            if (t->built) cudaEventDestroy(t->built);
+            cudaFreeAsync(t->mem, st);
+            delete t;
+            return sd_cuda_status(ce);
+        }
+    } else {
+        SdScalars hs;
+        ce = cudaMemcpyAsync(&hs, t->sc, sizeof(hs), cudaMemcpyDeviceToHost, st);
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+        if (ce == cudaSuccess) ce = cudaGetLastError();
+        int status = SD_OK;
+        if (ce != cudaSuccess) status = sd_cuda_status(ce);
+        else if (hs.status & ST_INDEX) status = SD_ERR_INDEX;
+        else if (hs.status & ST_NONFINITE) status = SD_ERR_NONFINITE;
+        if (status != SD_OK) {
+            cudaFreeAsync(t->mem, st);
+            delete t;
+            return status;
+        }
+        fill_info(t, hs);
+    }
 
     SdParams& P = t->P;
     int wrc = load_weight_basis(P);
-    if (wrc != SD_OK) { cudaFree(t->mem); delete t; return wrc; }
+    if (wrc != SD_OK) {
+        cudaStreamSynchronize(st);
+        if (t->built) cudaEventDestroy(t->built);
+        cudaFreeAsync(t->mem, st);
+        delete t;
+        return wrc;
+    }
     P.nodes = t->nodes;
     P.nw2 = t->nw2;
     P.hdr = t->hdr;
@@ -643,11 +774,11 @@ extern "C" int sd_build(const sd_geometry* g, float alpha, float beta, const sd_
     P.alpha2 = alpha * LOG2E;
     P.inv_alpha2 = 1.f / P.alpha2;
     P.S = S;
-    P.A_E = inf.A_E;
-    P.A_T = inf.A_T;
+    P.sc = t->sc;
     P.kw = t->paper_metric ? S / (alpha * alpha) : S / alpha;
     P.unit_weights = t->weights_unit;
     P.s_is_one = S == 1.f;
+    sd_mark_use(t, st);
     *out = t;
     return SD_OK;
 }
@@ -655,6 +786,15 @@ extern "C" int sd_build(const sd_geometry* g, float alpha, float beta, const sd_
 extern "C" int sd_tree_get_info(const sd_tree* t, sd_tree_info* info)
 {
     if (!t || !info) return SD_ERR_INVALID_ARG;
+    if (!t->info_ready) {
+        // a build with deferred checks: wait for it and read its scalars
+        sd_tree* m = const_cast<sd_tree*>(t);
+        SdScalars hs;
+        cudaError_t e = cudaEventSynchronize(t->built);
+        if (e == cudaSuccess) e = cudaMemcpy(&hs, t->sc, sizeof(hs), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return sd_cuda_status(e);
+        fill_info(m, hs);
+    }
     *info = t->info;
     return SD_OK;
 }
@@ -698,6 +838,16 @@ extern "C" int sd_tree_export(const sd_tree* t, sd_tree_view* v)
 extern "C" void sd_free(sd_tree* t)
 {
     if (!t) return;
+    // the memory is stream-ordered (cudaMallocAsync), and cudaFree does not
+    // wait for work still queued on it: wait for every recorded use first
+    for (int i = 0; i < t->n_use; ++i) {
+        cudaEventSynchronize(t->use_event[i]);
+        cudaEventDestroy(t->use_event[i]);
+    }
+    if (t->built) {
+        cudaEventSynchronize(t->built);
+        cudaEventDestroy(t->built);
+    }
     if (t->mem) cudaFree(t->mem);
     delete t;
 }

@@ -36,6 +36,16 @@ struct __align__(16) SdNode {
 enum { SD_KIND_POINT = 0, SD_KIND_SEG = 1, SD_KIND_TRI = 2 };
 enum { SD_HAS_PTS = 1, SD_HAS_SEGS = 2, SD_HAS_TRIS = 4 };
 
+// Tree scalars that the build computes on the device (read by the kernels,
+// copied to the host only when the tree's info is asked for).
+struct SdScalars {
+    float A_E, A_T;         // weight scales A of App. C.2 / C.3 (1 for unit weights)
+    float lo[3], inv_ex[3]; // scene box corner and 1 / extent (0 on a flat axis): query codes
+    float hi[3];
+    int status;             // build validation bits
+    int pad[2];
+};
+
 // Parameters a traversal needs, passed by value to the kernels.
 struct SdParams {
     const SdNode* nodes;
@@ -49,7 +59,7 @@ struct SdParams {
     float alpha2;         // alpha * log2(e): exponents are kept in base 2
     float inv_alpha2;     // 1 / alpha2
     float S;              // attenuation exponent
-    float A_E, A_T;       // scale A per kind (1 for unit weights)
+    const SdScalars* sc;  // device-computed scalars (A_E, A_T, scene box)
     float kw;             // S / alpha (S / alpha^2 with the alpha-scaled metric)
     int unit_weights;
     int s_is_one;
@@ -85,6 +95,25 @@ struct sd_tree {
     int32_t* leaf_count;  // nb
     float* params;        // 2n, original order
     int* status;          // device status word
+    SdScalars* sc;        // device scalars written at the end of the build
+    bool info_ready;      // info's device-derived fields (A, w_far, scene box) filled in
+    cudaEvent_t built;    // recorded after the build's last kernel (deferred checks)
+    // streams that have enqueued work on the tree and an event recorded after
+    // their latest such work: sd_free waits for these before releasing memory
+    cudaStream_t use_stream[4];
+    cudaEvent_t use_event[4];
+    int n_use, use_next;
+};
+
+// Record that `st` has enqueued work reading the tree (outside stream capture;
+// a captured graph's owner keeps the tree alive while the graph can run).
+void sd_mark_use(const sd_tree* t, cudaStream_t st);
+
+// Marks the tree's use on a stream when the enclosing API call returns.
+struct SdUse {
+    const sd_tree* t;
+    cudaStream_t st;
+    ~SdUse() { if (t) sd_mark_use(t, st); }
 };
 
 // ---------------------------------------------------------------------------
@@ -331,7 +360,7 @@ __device__ __forceinline__ void leaf_segment(const SdParams& P, float3 q, float4
     float wt = (u == 1.f && vv == 1.f) ? 1.f : edge_weight(t, u, vv, dw);
     float3 gwt = f3(0.f, 0.f, 0.f);
     if (GRAD && inside) gwt = scale(e, dw / ee);
-    apply_weight<GRAD>(P, P.A_E, dist, wt, gwt, gd, y, w, v);
+    apply_weight<GRAD>(P, __ldg(&P.sc->A_E), dist, wt, gwt, gd, y, w, v);
 }
 
 // Closest point of a triangle by its Voronoi regions (vertex, edge, face),
@@ -418,7 +447,7 @@ __device__ __forceinline__ void leaf_triangle(const SdParams& P, float3 q, float
         if (GRAD) gwt = f3(dw1 * gp1.x + dw2 * gp2.x, dw1 * gp1.y + dw2 * gp2.y, dw1 * gp1.z + dw2 * gp2.z);
         if (wt < 1e-6f) gwt = f3(0.f, 0.f, 0.f);
     }
-    apply_weight<GRAD>(P, P.A_T, dist, wt, gwt, gd, y, w, v);
+    apply_weight<GRAD>(P, __ldg(&P.sc->A_T), dist, wt, gwt, gd, y, w, v);
 }
 
 // one primitive at sorted position k

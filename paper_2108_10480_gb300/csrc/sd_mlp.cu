@@ -803,6 +803,7 @@ extern "C" int sd_lower_bound(const sd_tree* t, const float* q, int64_t M, float
                               int32_t* flag, void* stream)
 {
     if (!t || M < 0 || (M > 0 && !q)) return SD_ERR_INVALID_ARG;
+    SdUse use_{t, (cudaStream_t)stream};
     if (M == 0 || t->info.n_prims == 0) return SD_OK;
     if (M >= ((int64_t)1 << 31) / 3) return SD_ERR_TOO_LARGE;
     cudaStream_t st = (cudaStream_t)stream;
@@ -828,6 +829,7 @@ extern "C" int sd_surrogate_query(const sd_tree* t, const float* params, const f
                                   int64_t* n_routed, void* stream)
 {
     if (!t || !params || !frame || M < 0 || (M > 0 && (!q || !value))) return SD_ERR_INVALID_ARG;
+    SdUse use_{t, (cudaStream_t)stream};
     if (n_routed) *n_routed = 0;
     if (M == 0) return SD_OK;
     if (M >= ((int64_t)1 << 31) / 3) return SD_ERR_TOO_LARGE;

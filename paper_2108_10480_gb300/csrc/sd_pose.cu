@@ -192,6 +192,7 @@ extern "C" int sd_pose_query(const sd_tree* t, const float* X0, int64_t M, const
                              float* value, float* grad, const sd_query_opts* opts, void* stream)
 {
     if (!t || !pose || M < 0 || (M > 0 && (!X0 || !X || !value))) return SD_ERR_INVALID_ARG;
+    SdUse use_{t, (cudaStream_t)stream};
     for (int j = 0; j < 6; ++j)
         if (!std::isfinite(pose[j])) return SD_ERR_NONFINITE;
     if (M == 0) return SD_OK;
@@ -436,6 +437,7 @@ extern "C" int sd_batch_set_poses(sd_batch* bt, const double* poses, void* strea
 extern "C" int sd_batch_run(sd_batch* bt, float alpha_q, int32_t block, float* body_out, void* stream)
 {
     if (!bt || !body_out || !(alpha_q > 0.f) || !bt->posed) return SD_ERR_INVALID_ARG;
+    SdUse use_{bt->tree, (cudaStream_t)stream};
     cudaStream_t st = (cudaStream_t)stream;
     const int M = bt->M;
     k_batch_place<<<(M + 255) / 256, 256, 0, st>>>(bt->X0, bt->body_of, M, bt->poses, bt->X);

@@ -350,13 +350,13 @@ __global__ void k_fill_empty(float* value, float* grad, int M)
 // 24-bit Morton code of each query relative to the scene box (clamped), the
 // traversal order (8 bits per axis already give cells far smaller than a
 // packet's footprint; the order changes speed only, never results)
-__global__ void k_query_codes(const float* __restrict__ qs, int M, float3 lo, float3 inv_ext,
+__global__ void k_query_codes(const float* __restrict__ qs, int M, const SdScalars* __restrict__ sc,
                               unsigned* __restrict__ keys, int* __restrict__ vals)
 {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= M) return;
     float c[3] = {qs[3 * t], qs[3 * t + 1], qs[3 * t + 2]};
-    float l[3] = {lo.x, lo.y, lo.z}, ie[3] = {inv_ext.x, inv_ext.y, inv_ext.z};
+    float l[3] = {sc->lo[0], sc->lo[1], sc->lo[2]}, ie[3] = {sc->inv_ex[0], sc->inv_ex[1], sc->inv_ex[2]};
     unsigned k[3];
     for (int j = 0; j < 3; ++j) {
         float u = (c[j] - l[j]) * ie[j];
@@ -458,15 +458,12 @@ int compute_order(const sd_tree* t, const float* q, int m, int32_t* order, cudaS
     unsigned* k1 = k0 + m;
     int* v1 = (int*)(k1 + m);
     uint32_t* hist = (uint32_t*)(v1 + m);
-    const sd_tree_info& I = t->info;
-    float3 lo = make_float3(I.scene_lo[0], I.scene_lo[1], I.scene_lo[2]);
-    float ex[3];
-    for (int j = 0; j < 3; ++j) ex[j] = I.scene_hi[j] - I.scene_lo[j];
-    float3 ie = make_float3(ex[0] > 0 ? 1.f / ex[0] : 0.f, ex[1] > 0 ? 1.f / ex[1] : 0.f, ex[2] > 0 ? 1.f / ex[2] : 0.f);
     int nl = 1;
-    k_query_codes<<<(m + 255) / 256, 256, 0, st>>>(q, m, lo, ie, k0, order);
-    int where = sdsort::sort_pairs<unsigned, int>(k0, order, k1, v1, m, 24, hist, st, &nl);
-    if (where) cudaMemcpyAsync(order, v1, sizeof(int) * (size_t)m, cudaMemcpyDeviceToDevice, st);
+    // the sort's odd pass count leaves its result in the second buffer: give
+    // it `order` there and start from the scratch copy
+    k_query_codes<<<(m + 255) / 256, 256, 0, st>>>(q, m, t->sc, k0, v1);
+    int where = sdsort::sort_pairs<unsigned, int>(k0, v1, k1, order, m, 24, hist, st, &nl);
+    if (!where) cudaMemcpyAsync(order, v1, sizeof(int) * (size_t)m, cudaMemcpyDeviceToDevice, st);
     sd_count_launches(nl);
     e = cudaGetLastError();
     cudaFreeAsync(tmp, st);
@@ -479,6 +476,7 @@ extern "C" int sd_query_order(const sd_tree* t, const float* q, int64_t M, int32
 {
     int rc = check_query_args(t, q, M, order ? (const float*)order : nullptr);
     if (rc != SD_OK) return rc;
+    SdUse use_{t, (cudaStream_t)stream};
     if (M == 0) return SD_OK;
     cudaStream_t st = (cudaStream_t)stream;
     int m = (int)M;
@@ -494,6 +492,7 @@ extern "C" int sd_query(const sd_tree* t, const float* q, int64_t M, float* valu
 {
     int rc = check_query_args(t, q, M, value);
     if (rc != SD_OK) return rc;
+    SdUse use_{t, (cudaStream_t)stream};
     sd_query_opts opts;
     if (opts_in) opts = *opts_in; else sd_default_query_opts(&opts);
     if (opts.block < 0 || opts.block > PK_MAX_THREADS || (opts.block % 32) != 0) return SD_ERR_INVALID_ARG;
@@ -533,6 +532,7 @@ extern "C" int sd_query_brute(const sd_tree* t, const float* q, int64_t M, float
     (void)opts;
     int rc = check_query_args(t, q, M, value);
     if (rc != SD_OK) return rc;
+    SdUse use_{t, (cudaStream_t)stream};
     if (M == 0) return SD_OK;
     cudaStream_t st = (cudaStream_t)stream;
     int m = (int)M;
@@ -601,6 +601,7 @@ extern "C" int sd_query_noalloc(const sd_tree* t, const float* q, int64_t M, flo
 {
     int rc = check_query_args(t, q, M, value);
     if (rc != SD_OK) return rc;
+    SdUse use_{t, (cudaStream_t)stream};
     if (M > SD_NOALLOC_MAX_QUERIES) return SD_ERR_TOO_LARGE;
     if (M == 0) return SD_OK;
     int dev = 0;
@@ -639,13 +640,7 @@ extern "C" int sd_query_noalloc(const sd_tree* t, const float* q, int64_t M, flo
     const int* order = nullptr;
     int nl = 0;
     if (m > 1) {
-        const sd_tree_info& I = t->info;
-        float3 lo = make_float3(I.scene_lo[0], I.scene_lo[1], I.scene_lo[2]);
-        float ex[3];
-        for (int j = 0; j < 3; ++j) ex[j] = I.scene_hi[j] - I.scene_lo[j];
-        float3 ie = make_float3(ex[0] > 0 ? 1.f / ex[0] : 0.f, ex[1] > 0 ? 1.f / ex[1] : 0.f,
-                                ex[2] > 0 ? 1.f / ex[2] : 0.f);
-        k_query_codes<<<(m + 255) / 256, 256, 0, st>>>(q, m, lo, ie, k0, ord0);
+        k_query_codes<<<(m + 255) / 256, 256, 0, st>>>(q, m, t->sc, k0, ord0);
         ++nl;
         int where = sdsort::sort_pairs<unsigned, int>(k0, ord0, k1, ord1, m, 24, hist, st, &nl);
         order = where ? ord1 : ord0;
@@ -674,15 +669,12 @@ int order_into(const sd_tree* t, const float* q, int m, int32_t* order, void* sc
     unsigned* k1 = k0 + m;
     int* v1 = (int*)(k1 + m);
     uint32_t* hist = (uint32_t*)(v1 + m);
-    const sd_tree_info& I = t->info;
-    float3 lo = make_float3(I.scene_lo[0], I.scene_lo[1], I.scene_lo[2]);
-    float ex[3];
-    for (int j = 0; j < 3; ++j) ex[j] = I.scene_hi[j] - I.scene_lo[j];
-    float3 ie = make_float3(ex[0] > 0 ? 1.f / ex[0] : 0.f, ex[1] > 0 ? 1.f / ex[1] : 0.f, ex[2] > 0 ? 1.f / ex[2] : 0.f);
     int nl = 1;
-    k_query_codes<<<(m + 255) / 256, 256, 0, st>>>(q, m, lo, ie, k0, order);
-    int where = sdsort::sort_pairs<unsigned, int>(k0, order, k1, v1, m, 24, hist, st, &nl);
-    if (where) cudaMemcpyAsync(order, v1, sizeof(int) * (size_t)m, cudaMemcpyDeviceToDevice, st);
+    // the sort's odd pass count leaves its result in the second buffer: give
+    // it `order` there and start from the scratch copy
+    k_query_codes<<<(m + 255) / 256, 256, 0, st>>>(q, m, t->sc, k0, v1);
+    int where = sdsort::sort_pairs<unsigned, int>(k0, v1, k1, order, m, 24, hist, st, &nl);
+    if (!where) cudaMemcpyAsync(order, v1, sizeof(int) * (size_t)m, cudaMemcpyDeviceToDevice, st);
     sd_count_launches(nl);
     return sd_cuda_status(cudaGetLastError());
 }

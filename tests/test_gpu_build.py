@@ -86,3 +86,26 @@ def test_single_primitive_and_empty():
     e = _gpu(alpha=10.0, beta=0.5)
     v, gr = e.query(torch.zeros(5, 3, device="cuda"))
     assert torch.isinf(v).all() and (gr == 0).all()
+
+
+def test_deferred_checks():
+    """check=False enqueues the same build without waiting: identical tree,
+    identical query results, and invalid input reported by status()."""
+    V, F = synth.icosphere(3)
+    q = torch.from_numpy(synth.uniform_box(5000, [-1.5] * 3, [1.5] * 3, 3)).cuda()
+    a = _gpu(tris=(V, F), alpha=50.0, beta=0.5)
+    b = _gpu(tris=(V, F), alpha=50.0, beta=0.5, check=False)
+    va, ga = a.query(q)
+    vb, gb = b.query(q)
+    assert b.status() == 0
+    assert torch.equal(va, vb) and torch.equal(ga, gb)
+    assert a.info() == b.info()
+    F2 = F.copy()
+    F2[3, 2] = V.shape[0]
+    c = _gpu(tris=(V, F2), alpha=10.0, beta=0.5, check=False)
+    assert c.status() == 5
+    P = synth.points_on_sphere(100, 0.0, 0)
+    P[17, 1] = np.nan
+    d = _gpu(points=P, alpha=10.0, beta=0.5, check=False)
+    assert d.status() == 4
+    assert d.status() == 0          # reading the status clears it
