@@ -36,7 +36,8 @@ typedef enum {
     SD_ERR_OOM = 3,         /* device allocation failed */
     SD_ERR_NONFINITE = 4,   /* a vertex or query coordinate is NaN/Inf */
     SD_ERR_INDEX = 5,       /* an edge/triangle index is outside its vertex array */
-    SD_ERR_TOO_LARGE = 6    /* a size exceeds what the library supports (2^31-1 primitives) */
+    SD_ERR_TOO_LARGE = 6,   /* a size exceeds what the library supports (2^31-1 primitives) */
+    SD_ERR_TIMEOUT = 7      /* a bounded device-side wait ran out (the results of that call are invalid) */
 } sd_status;
 
 /* Geometry of the data mesh M_d = (V, F) (Sec. 3). Each part may be empty
@@ -137,7 +138,7 @@ int sd_query_brute(const sd_tree* t, const float* q, int64_t M, float* value, fl
  * part-way. Same inputs and outputs as sd_query with default options
  * (Morton-ordered traversal, value and gradient, no counts).
  *   M      0 <= M <= 262144 (SD_ERR_TOO_LARGE beyond, nothing launched)
- * Its temporary storage (about 4.5 MB) is one static device array that
+ * Its temporary storage (about 4.8 MB) is one static device array that
  * every device loading the library keeps until the process exits. All
  * calls on a device share it, so calls that overlap on the GPU race; calls
  * ordered on one stream are safe. The first call on a device looks up the

@@ -14,7 +14,8 @@ c_void_p, c_int64, c_int32, c_float, c_double = (ctypes.c_void_p, ctypes.c_int64
 
 SD_OK = 0
 STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "out of device memory",
-          4: "non-finite coordinate", 5: "primitive index out of range", 6: "size too large"}
+          4: "non-finite coordinate", 5: "primitive index out of range", 6: "size too large",
+          7: "device wait timed out"}
 
 
 class SdPoints(ctypes.Structure):

@@ -59,6 +59,7 @@ extern "C" const char* sd_status_str(int s)
     case SD_ERR_NONFINITE: return "non-finite coordinate";
     case SD_ERR_INDEX: return "primitive index out of range";
     case SD_ERR_TOO_LARGE: return "size too large";
+    case SD_ERR_TIMEOUT: return "device wait timed out";
     default: return "unknown status";
     }
 }

@@ -18,7 +18,7 @@
 
 namespace {
 
-enum { ST_NONFINITE = 1, ST_INDEX = 2 };
+enum { ST_NONFINITE = 1, ST_INDEX = 2, ST_TIMEOUT = 4 };
 
 // scalars the build accumulates on the device
 struct BuildScalars {
@@ -438,6 +438,7 @@ __global__ void k_finalize(const BuildScalars* bs, int n, int unit, SdScalars* s
     }
     sc->status = bs->status;
     if (bs->status & ST_INDEX) atomicOr(status, 1 << SD_ERR_INDEX);
+    if (bs->status & ST_TIMEOUT) atomicOr(status, 1 << SD_ERR_TIMEOUT);
     if (bs->status & ST_NONFINITE) atomicOr(status, 1 << SD_ERR_NONFINITE);
 }
 
@@ -695,7 +696,8 @@ extern "C" int sd_build(const sd_geometry* g, float alpha, float beta, const sd_
         // Morton order
         ++nl;
         k_morton<<<nblk(n, T), T, 0, st>>>(geo, bs, (unsigned long long*)t->codes, k0, v0);
-        int where = sdsort::sort_pairs<unsigned long long, int>(k0, v0, k1, v1, n, 64, hist, st, &nl);
+        int where = sdsort::sort_pairs<unsigned long long, int>(k0, v0, k1, v1, n, 64, hist, &bs->status,
+                                                                 ST_TIMEOUT, st, &nl);
         unsigned long long* sk = where ? k1 : k0;
         int* sv = where ? v1 : v0;
         // topology
@@ -745,6 +747,7 @@ extern "C" int sd_build(const sd_geometry* g, float alpha, float beta, const sd_
         if (ce != cudaSuccess) status = sd_cuda_status(ce);
         else if (hs.status & ST_INDEX) status = SD_ERR_INDEX;
         else if (hs.status & ST_NONFINITE) status = SD_ERR_NONFINITE;
+        else if (hs.status & ST_TIMEOUT) status = SD_ERR_TIMEOUT;
         if (status != SD_OK) {
             cudaFreeAsync(t->mem, st);
             delete t;

@@ -838,7 +838,7 @@ extern "C" int sd_surrogate_query(const sd_tree* t, const float* params, const f
     if (t->info.n_prims == 0) return sd_query(t, q, M, value, grad, nullptr, stream);
     // scratch: flags, sort keys/values, gathered queries and results
     size_t bytes = sizeof(int) * 8 * (size_t)m + sizeof(float) * 11 * (size_t)m +
-                   sizeof(uint32_t) * (256 * ((size_t)m / 1024 + 1) + 8 * 256) + 4096;
+                   sizeof(uint32_t) * sdsort::hist_words(m, 1) + 4096;
     void* tmp = nullptr;
     cudaError_t e = cudaMallocAsync(&tmp, bytes, st);
     if (e != cudaSuccess) { cudaGetLastError(); return SD_ERR_OOM; }
@@ -860,7 +860,7 @@ extern "C" int sd_surrogate_query(const sd_tree* t, const float* params, const f
     k_iota_flagkey<<<(m + 255) / 256, 256, 0, st>>>(flag, m, k0, v0, cnt);
     int nl = 1;
     // stable partition: exact queries first, surrogate queries after
-    int where = sdsort::sort_pairs<unsigned, int>(k0, v0, k1, v1, m, 1, hist, st, &nl);
+    int where = sdsort::sort_pairs<unsigned, int>(k0, v0, k1, v1, m, 1, hist, t->status, 1 << SD_ERR_TIMEOUT, st, &nl);
     int* idx = where ? v1 : v0;
     int hcnt = 0;
     e = cudaMemcpyAsync(&hcnt, cnt, sizeof(int), cudaMemcpyDeviceToHost, st);

@@ -449,7 +449,7 @@ namespace {
 // Morton order of the queries into `order` (stream-ordered scratch).
 int compute_order(const sd_tree* t, const float* q, int m, int32_t* order, cudaStream_t st)
 {
-    size_t hw = sdsort::hist_words(m);
+    size_t hw = sdsort::hist_words(m, 3);
     size_t bytes = sizeof(unsigned) * 2 * (size_t)m + sizeof(int) * (size_t)m + sizeof(uint32_t) * hw + 1024;
     void* tmp = nullptr;
     cudaError_t e = cudaMallocAsync(&tmp, bytes, st);
@@ -462,7 +462,8 @@ int compute_order(const sd_tree* t, const float* q, int m, int32_t* order, cudaS
     // the sort's odd pass count leaves its result in the second buffer: give
     // it `order` there and start from the scratch copy
     k_query_codes<<<(m + 255) / 256, 256, 0, st>>>(q, m, t->sc, k0, v1);
-    int where = sdsort::sort_pairs<unsigned, int>(k0, v1, k1, order, m, 24, hist, st, &nl);
+    int where = sdsort::sort_pairs<unsigned, int>(k0, v1, k1, order, m, 24, hist, t->status, 1 << SD_ERR_TIMEOUT,
+                                                  st, &nl);
     if (!where) cudaMemcpyAsync(order, v1, sizeof(int) * (size_t)m, cudaMemcpyDeviceToDevice, st);
     sd_count_launches(nl);
     e = cudaGetLastError();
@@ -583,8 +584,7 @@ extern "C" int sd_query_status(const sd_tree* t, void* stream)
 namespace {
 
 constexpr int SD_NOALLOC_MAX_QUERIES = 262144;
-constexpr size_t NOALLOC_TILES = (SD_NOALLOC_MAX_QUERIES + sdsort::TILE - 1) / sdsort::TILE;
-constexpr size_t NOALLOC_HIST_WORDS = 256 * NOALLOC_TILES + 8 * 256;
+constexpr size_t NOALLOC_HIST_WORDS = sdsort::hist_words(SD_NOALLOC_MAX_QUERIES, 3);
 // [counter: 256 B][keys: 2 x max u32][order, alternate order: 2 x max i32][sort counters]
 constexpr size_t NOALLOC_BYTES = 256 + 4 * sizeof(uint32_t) * (size_t)SD_NOALLOC_MAX_QUERIES +
                                  sizeof(uint32_t) * NOALLOC_HIST_WORDS;
@@ -642,7 +642,8 @@ extern "C" int sd_query_noalloc(const sd_tree* t, const float* q, int64_t M, flo
     if (m > 1) {
         k_query_codes<<<(m + 255) / 256, 256, 0, st>>>(q, m, t->sc, k0, ord0);
         ++nl;
-        int where = sdsort::sort_pairs<unsigned, int>(k0, ord0, k1, ord1, m, 24, hist, st, &nl);
+        int where = sdsort::sort_pairs<unsigned, int>(k0, ord0, k1, ord1, m, 24, hist, t->status,
+                                                      1 << SD_ERR_TIMEOUT, st, &nl);
         order = where ? ord1 : ord0;
     }
     dispatch<false>(t, q, m, order, value, grad, nullptr, 0, work, st);
@@ -657,7 +658,7 @@ namespace sdint {
 
 size_t order_scratch_bytes(int m)
 {
-    return sizeof(unsigned) * 2 * (size_t)m + sizeof(int) * (size_t)m + sizeof(uint32_t) * sdsort::hist_words(m) + 256;
+    return sizeof(unsigned) * 2 * (size_t)m + sizeof(int) * (size_t)m + sizeof(uint32_t) * sdsort::hist_words(m, 3) + 256;
 }
 
 // Morton order of m queries into `order`, using caller scratch of
@@ -673,7 +674,8 @@ int order_into(const sd_tree* t, const float* q, int m, int32_t* order, void* sc
     // the sort's odd pass count leaves its result in the second buffer: give
     // it `order` there and start from the scratch copy
     k_query_codes<<<(m + 255) / 256, 256, 0, st>>>(q, m, t->sc, k0, v1);
-    int where = sdsort::sort_pairs<unsigned, int>(k0, v1, k1, order, m, 24, hist, st, &nl);
+    int where = sdsort::sort_pairs<unsigned, int>(k0, v1, k1, order, m, 24, hist, t->status, 1 << SD_ERR_TIMEOUT,
+                                                  st, &nl);
     if (!where) cudaMemcpyAsync(order, v1, sizeof(int) * (size_t)m, cudaMemcpyDeviceToDevice, st);
     sd_count_launches(nl);
     return sd_cuda_status(cudaGetLastError());

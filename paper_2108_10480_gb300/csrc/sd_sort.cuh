@@ -1,12 +1,21 @@
-// Stable LSD radix sort (8-bit digits) of key/value pairs in device memory.
-// Per pass: a per-tile digit histogram (plus digit totals), an exclusive
-// scan over (digit, tile) with one block per digit, and a stable scatter
-// that ranks equal digits inside a tile with warp match masks. Used for the Morton order of primitives (64-bit
-// keys) and of queries (32-bit keys).
+// Stable LSD radix sort (8-bit digits) of key/value pairs in device memory,
+// one launch per digit pass ("onesweep"): a first kernel counts every
+// digit of every pass at once; each pass kernel then takes tiles in
+// launch order from an atomic counter, publishes its tile's digit counts,
+// finds the counts of all earlier tiles by a decoupled look-back over their
+// published (count, flag) words, and scatters its keys stably (equal digits
+// ranked inside the tile with warp match masks). Used for the Morton order
+// of primitives (64-bit keys) and of queries (32-bit keys).
+//
+// The look-back only waits on tiles with smaller indices, which were taken
+// by blocks that already run; every wait is bounded all the same, and a wait
+// that runs out sets the error word (the sort's result is then invalid).
 #pragma once
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <algorithm>
 
 namespace sdsort {
 
@@ -14,110 +23,129 @@ constexpr int THREADS = 256;
 constexpr int ITEMS = 4;
 constexpr int TILE = THREADS * ITEMS;
 constexpr int WARPS = THREADS / 32;
+constexpr int MAX_PASSES = 8;
+constexpr uint32_t FLAG_AGG = 1u << 30;     // the tile's own counts
+constexpr uint32_t FLAG_PRE = 2u << 30;     // counts of tiles 0..i inclusive
+constexpr uint32_t VALUE = FLAG_AGG - 1u;
+constexpr int SPIN_LIMIT = 1 << 21;
 
-template <typename K>
-__global__ void __launch_bounds__(THREADS) hist_kernel(const K* __restrict__ keys, int n, int shift,
-                                                       uint32_t* __restrict__ hist, int ntiles,
-                                                       uint32_t* __restrict__ tot)
+// scratch words for sorting n keys in `passes` passes: per pass the
+// (tile, digit) look-back words and 256 digit totals, then one tile counter
+// per pass and an error word
+constexpr size_t hist_words(size_t n, int passes = MAX_PASSES)
 {
-    __shared__ uint32_t h[256];
-    h[threadIdx.x] = 0;
-    __syncthreads();
-    int base = blockIdx.x * TILE;
-#pragma unroll
-    for (int r = 0; r < ITEMS; ++r) {
-        int i = base + r * THREADS + threadIdx.x;
-        if (i < n) atomicAdd(&h[(unsigned)(keys[i] >> shift) & 255u], 1u);
-    }
-    __syncthreads();
-    uint32_t c = h[threadIdx.x];
-    hist[threadIdx.x * ntiles + blockIdx.x] = c;
-    if (c) atomicAdd(&tot[threadIdx.x], c);
+    return (size_t)passes * 256 * ((n + TILE - 1) / TILE) + (size_t)passes * 256 + 64;
 }
 
-// Exclusive scan of the (digit, tile) counters, one block per digit: the
-// digit's base is the sum of the totals of all smaller digits, and the
-// block scans its row of per-tile counts (contiguous in memory).
-static __global__ void __launch_bounds__(256) scan_rows_kernel(uint32_t* __restrict__ hist, int ntiles,
-                                                              const uint32_t* __restrict__ tot)
+// digit totals of every pass
+template <typename K>
+__global__ void __launch_bounds__(THREADS) count_kernel(const K* __restrict__ keys, int n, int passes,
+                                                        uint32_t* __restrict__ totals)
 {
-    __shared__ uint32_t wsum[8];
-    __shared__ uint32_t sbase;
-    const int d = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (warp == 0) {
-        uint32_t acc = 0;
-        for (int k = lane; k < d; k += 32) acc += tot[k];
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (lane == 0) sbase = acc;
+    __shared__ uint32_t h[MAX_PASSES][256];
+    for (int p = 0; p < passes; ++p) h[p][threadIdx.x] = 0;
+    __syncthreads();
+    for (int i = blockIdx.x * THREADS + threadIdx.x; i < n; i += gridDim.x * THREADS) {
+        K k = keys[i];
+        for (int p = 0; p < passes; ++p) atomicAdd(&h[p][(unsigned)(k >> (8 * p)) & 255u], 1u);
     }
     __syncthreads();
-    uint32_t carry = sbase;
-    uint32_t* row = hist + (size_t)d * ntiles;
-    for (int c0 = 0; c0 < ntiles; c0 += 256 * 8) {
-        int b = c0 + tid * 8;
-        uint32_t v[8];
-        uint32_t s = 0;
+    for (int p = 0; p < passes; ++p) {
+        uint32_t c = h[p][threadIdx.x];
+        if (c) atomicAdd(&totals[256 * p + threadIdx.x], c);
+    }
+}
+
+__device__ __forceinline__ uint32_t load_volatile(const uint32_t* p) { return *(const volatile uint32_t*)p; }
+
+template <typename K, typename V>
+__global__ void __launch_bounds__(THREADS) pass_kernel(const K* __restrict__ kin, const V* __restrict__ vin,
+                                                       K* __restrict__ kout, V* __restrict__ vout, int n, int shift,
+                                                       const uint32_t* __restrict__ totals, uint32_t* look,
+                                                       int* tile_counter, int* err, int err_bits)
+{
+    __shared__ int s_tile;
+    __shared__ uint32_t s_cnt[256];
+    __shared__ uint32_t s_base[256];
+    __shared__ uint32_t s_wsum[WARPS];
+    __shared__ uint32_t run[256];
+    __shared__ uint32_t cnt[WARPS][256];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) s_tile = atomicAdd(tile_counter, 1);
+    s_cnt[tid] = 0;
+    run[tid] = 0;
+    __syncthreads();
+    const int tile = s_tile;
+    const int base = tile * TILE;
+    K key[ITEMS];
+    unsigned dig[ITEMS];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            v[k] = (b + k < ntiles) ? row[b + k] : 0u;
-            s += v[k];
+    for (int r = 0; r < ITEMS; ++r) {
+        int i = base + r * THREADS + tid;
+        bool valid = i < n;
+        key[r] = valid ? kin[i] : K(0);
+        dig[r] = valid ? ((unsigned)(key[r] >> shift) & 255u) : 256u + (unsigned)lane;
+        if (valid) atomicAdd(&s_cnt[dig[r]], 1u);
+    }
+    __syncthreads();
+    // publish this tile's counts, then look back for the earlier tiles'
+    const uint32_t local = s_cnt[tid];
+    uint32_t* mine = look + (size_t)tile * 256 + tid;
+    atomicExch(mine, (tile == 0 ? FLAG_PRE : FLAG_AGG) | local);
+    uint32_t excl = 0;
+    if (tile > 0) {
+        int j = tile - 1;
+        int spins = 0;
+        while (j >= 0) {
+            uint32_t w = load_volatile(look + (size_t)j * 256 + tid);
+            uint32_t f = w & ~VALUE;
+            if (f == 0u) {
+                if (++spins > SPIN_LIMIT) {
+                    atomicOr(err, err_bits);
+                    break;
+                }
+                continue;
+            }
+            excl += w & VALUE;
+            if (f == FLAG_PRE) break;
+            --j;
         }
-        uint32_t x = s;
+        atomicExch(mine, FLAG_PRE | (excl + local));
+    }
+    // digit base: exclusive scan of the pass's digit totals
+    {
+        uint32_t t = totals[tid];
+        uint32_t x = t;
         for (int o = 1; o < 32; o <<= 1) {
             uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
             if (lane >= o) x += y;
         }
-        if (lane == 31) wsum[warp] = x;
+        if (lane == 31) s_wsum[warp] = x;
         __syncthreads();
-        uint32_t wpre = 0, total = 0;
-#pragma unroll
-        for (int w = 0; w < 8; ++w) {
-            uint32_t ws = wsum[w];
-            if (w < warp) wpre += ws;
-            total += ws;
-        }
-        uint32_t run = carry + wpre + x - s;
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            if (b + k < ntiles) row[b + k] = run;
-            run += v[k];
-        }
-        carry += total;
-        __syncthreads();
+        uint32_t wpre = 0;
+        for (int w = 0; w < warp; ++w) wpre += s_wsum[w];
+        s_base[tid] = wpre + x - t + excl;
     }
-}
-
-template <typename K, typename V>
-__global__ void __launch_bounds__(THREADS) scatter_kernel(const K* __restrict__ kin, const V* __restrict__ vin,
-                                                          K* __restrict__ kout, V* __restrict__ vout, int n,
-                                                          int shift, const uint32_t* __restrict__ hist, int ntiles)
-{
-    __shared__ uint32_t goff[256];
-    __shared__ uint32_t run[256];
-    __shared__ uint32_t cnt[WARPS][256];
-    int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    goff[tid] = hist[tid * ntiles + blockIdx.x];
-    run[tid] = 0;
-    unsigned lt = (1u << lane) - 1u;
-    int base = blockIdx.x * TILE;
+    __syncthreads();
+    // stable scatter: rounds of THREADS keys in order, ranked by warp and lane
+    const unsigned lt = (1u << lane) - 1u;
+#pragma unroll
     for (int r = 0; r < ITEMS; ++r) {
 #pragma unroll
         for (int w = 0; w < WARPS; ++w) cnt[w][tid] = 0;
         __syncthreads();
-        int i = base + r * THREADS + tid;
-        bool valid = i < n;
-        K key = valid ? kin[i] : K(0);
-        unsigned d = valid ? ((unsigned)(key >> shift) & 255u) : 256u + (unsigned)lane;
+        const int i = base + r * THREADS + tid;
+        const bool valid = i < n;
+        const unsigned d = dig[r];
         unsigned peers = __match_any_sync(0xffffffffu, d);
         unsigned rank = __popc(peers & lt);
-        bool leader = (peers & lt) == 0u;
-        if (valid && leader) cnt[warp][d] = __popc(peers);
+        if (valid && (peers & lt) == 0u) cnt[warp][d] = __popc(peers);
         __syncthreads();
         if (valid) {
             uint32_t pre = run[d];
             for (int w = 0; w < warp; ++w) pre += cnt[w][d];
-            uint32_t dst = goff[d] + pre + rank;
-            kout[dst] = key;
+            uint32_t dst = s_base[d] + pre + rank;
+            kout[dst] = key[r];
             vout[dst] = vin[i];
         }
         __syncthreads();
@@ -129,35 +157,34 @@ __global__ void __launch_bounds__(THREADS) scatter_kernel(const K* __restrict__ 
     }
 }
 
-// counters for one sort: per-(digit, tile) counts, then 8 x 256 digit totals
-inline size_t hist_words(int n) { return (size_t)256 * (size_t)((n + TILE - 1) / TILE) + 8 * 256; }
-
-// Sorts (k0, v0) by the low `bits` bits of the key (a multiple of 8 is not
-// required; passes cover ceil(bits / 8) digits). Uses (k1, v1) as the
-// alternate buffers; returns 0 if the result ends in (k0, v0), 1 if in
-// (k1, v1). hist needs hist_words(n) words. Adds the number of kernel
-// launches to *launches.
+// Sorts (k0, v0) by the low `bits` bits of the key (ceil(bits / 8) passes).
+// Uses (k1, v1) as the alternate buffers; returns 0 if the result ends in
+// (k0, v0), 1 if in (k1, v1). scratch needs hist_words(n, passes) words;
+// err_bits are or-ed into the device int *err if a look-back wait ran out.
+// Adds the number of kernel launches to *launches.
 template <typename K, typename V>
-int sort_pairs(K* k0, V* v0, K* k1, V* v1, int n, int bits, uint32_t* hist, cudaStream_t st, int* launches)
+int sort_pairs(K* k0, V* v0, K* k1, V* v1, int n, int bits, uint32_t* scratch, int* err, int err_bits,
+               cudaStream_t st, int* launches)
 {
     if (n <= 1) return 0;
-    int ntiles = (n + TILE - 1) / TILE;
-    int passes = (bits + 7) / 8;
-    uint32_t* tot = hist + (size_t)256 * ntiles;
-    cudaMemsetAsync(tot, 0, sizeof(uint32_t) * 256 * passes, st);
+    const int ntiles = (n + TILE - 1) / TILE;
+    const int passes = (bits + 7) / 8;
+    uint32_t* look = scratch;
+    uint32_t* totals = look + (size_t)passes * 256 * ntiles;
+    int* counters = (int*)(totals + (size_t)passes * 256);
+    cudaMemsetAsync(scratch, 0, sizeof(uint32_t) * hist_words(n, passes), st);
+    count_kernel<K><<<std::min(ntiles, 1024), THREADS, 0, st>>>(k0, n, passes, totals);
     int cur = 0;
     for (int p = 0; p < passes; ++p) {
-        int shift = 8 * p;
         const K* ki = cur ? k1 : k0;
         const V* vi = cur ? v1 : v0;
         K* ko = cur ? k0 : k1;
         V* vo = cur ? v0 : v1;
-        hist_kernel<K><<<ntiles, THREADS, 0, st>>>(ki, n, shift, hist, ntiles, tot + 256 * p);
-        scan_rows_kernel<<<256, 256, 0, st>>>(hist, ntiles, tot + 256 * p);
-        scatter_kernel<K, V><<<ntiles, THREADS, 0, st>>>(ki, vi, ko, vo, n, shift, hist, ntiles);
+        pass_kernel<K, V><<<ntiles, THREADS, 0, st>>>(ki, vi, ko, vo, n, 8 * p, totals + 256 * p,
+                                                      look + (size_t)p * 256 * ntiles, counters + p, err, err_bits);
         cur ^= 1;
-        *launches += 3;
     }
+    *launches += 1 + passes;
     return cur;
 }
 
