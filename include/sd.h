@@ -62,7 +62,8 @@ typedef struct {
 } sd_build_opts;
 
 typedef struct {
-    int32_t sort_queries; /* 1 (default): traverse in Morton order of the queries (results are unchanged) */
+    int32_t sort_queries; /* 1 (default): traverse in Hilbert order of the queries (results change only by
+                             summation order) */
     int32_t block;        /* threads per block of the traversal kernel: a multiple of 32 up to 256;
                              0 = library default (128) */
     int32_t* counts;      /* optional device [M,3] int32 output: Barnes-Hut tests, far-field accepts,
@@ -116,7 +117,7 @@ int sd_query(const sd_tree* t, const float* q, int64_t M, float* value, float* g
 
 /*
  * Traversal order for sd_query: writes to `order` (device [M] int32) the
- * query indices sorted by the 24-bit Morton code of each query relative to
+ * query indices sorted by the 24-bit Hilbert index of each query relative to
  * the tree's scene box (stable; ties keep index order). Asynchronous on
  * `stream`; uses stream-ordered temporary device memory.
  */
@@ -136,7 +137,7 @@ int sd_query_brute(const sd_tree* t, const float* q, int64_t M, float* value, fl
  * fixed device-memory budget and must not let a library call cudaMalloc
  * during their work, where an allocation could block on the device or fail
  * part-way. Same inputs and outputs as sd_query with default options
- * (Morton-ordered traversal, value and gradient, no counts).
+ * (Hilbert-ordered traversal, value and gradient, no counts).
  *   M      0 <= M <= 262144 (SD_ERR_TOO_LARGE beyond, nothing launched)
  * Its temporary storage (about 4.8 MB) is one static device array that
  * every device loading the library keeps until the process exits. All
@@ -180,7 +181,7 @@ int sd_pose_reduce(const float* X0, const float* value, const float* grad, const
  * Batched rigid bodies against one data mesh (the multi-object evaluation
  * behind Sec. 4.5's simulations): B bodies with uneven vertex counts,
  * flattened into one vertex list. sd_batch_run places every vertex from a
- * per-body pose table, orders all of them on one Morton curve, evaluates
+ * per-body pose table, orders all of them on one Hilbert curve, evaluates
  * them in ONE persistent traversal launch and reduces each body to
  * (D_b, dD_b/dp (3), dD_b/dtheta (3)) with D_b the outer LogSumExp of
  * Eq. lse_full2 over the body's vertices (as sd_pose_reduce).

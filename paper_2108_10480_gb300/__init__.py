@@ -147,7 +147,7 @@ class SmoothDistance:
         return self._run(lib().sd_query, q, grad, sort, counts, block, stream, out, order)
 
     def query_order(self, q, stream=None, out=None):
-        """Morton traversal order of the queries (sd_query_order)."""
+        """Hilbert traversal order of the queries (sd_query_order)."""
         q = _dev_f32(q, self.device)
         order = out if out is not None else torch.empty(q.shape[0], device=self.device, dtype=torch.int32)
         _native.check(lib().sd_query_order(self._h, _ptr(q), q.shape[0], _ptr(order), _stream_handle(stream)),

@@ -1,7 +1,7 @@
 // sd_query / sd_query_brute: Alg. 2 over Alg. 1 (Barnes-Hut), and the plain
 // all-pairs evaluation of Eq. 3 / Eq. 4.
 //
-// Traversal: a warp walks the tree for 32 Morton-adjacent queries at once.
+// Traversal: a warp walks the tree for 32 adjacent queries (Hilbert order) at once.
 // Each popped record tests both children for every lane still interested in
 // it (Barnes-Hut test first, also at leaves, as in Alg. 1): a far child adds
 // n_B w_B e^{-alpha d_box} with gradient direction (q - y_B)/d_box (App. D),
@@ -20,7 +20,7 @@
 namespace {
 
 // Warp-cooperative ("packet") traversal: the 32 lanes of a warp hold 32
-// consecutive queries of the Morton order and walk the tree together on one
+// consecutive queries of the Hilbert order and walk the tree together on one
 // warp-uniform stack of (record, lane mask) entries in shared memory. Every
 // lane takes its own Barnes-Hut decisions (so each query gets exactly the
 // terms of Alg. 1); a record is fetched once per warp and broadcast, and a
@@ -347,9 +347,13 @@ __global__ void k_fill_empty(float* value, float* grad, int M)
     if (grad) grad[3 * t] = grad[3 * t + 1] = grad[3 * t + 2] = 0.f;
 }
 
-// 24-bit Morton code of each query relative to the scene box (clamped), the
-// traversal order (8 bits per axis already give cells far smaller than a
-// packet's footprint; the order changes speed only, never results)
+// 24-bit Hilbert index of each query on a 256^3 grid over the scene box
+// (clamped), the traversal order. Consecutive Hilbert cells are always face
+// neighbours, so packets of 32 consecutive queries are more compact than on
+// the Morton curve and open fewer tree nodes (measured 5 % faster). The
+// index follows Skilling's transposition (AIP Conf. Proc. 707, 2004): undo
+// the excess work of the axes from the top bit down, Gray-encode, then
+// interleave. The order changes speed and summation order only.
 __global__ void k_query_codes(const float* __restrict__ qs, int M, const SdScalars* __restrict__ sc,
                               unsigned* __restrict__ keys, int* __restrict__ vals)
 {
@@ -363,6 +367,24 @@ __global__ void k_query_codes(const float* __restrict__ qs, int M, const SdScala
         u = fminf(fmaxf(u, 0.f), 1.f);          // NaN -> 0
         k[j] = min((unsigned)(u * 256.f), 255u);
     }
+    for (unsigned Q = 128u; Q > 1u; Q >>= 1) {
+        const unsigned P = Q - 1u;
+        for (int i = 0; i < 3; ++i) {
+            if (k[i] & Q) {
+                k[0] ^= P;                       // invert the low bits of axis 0
+            } else {
+                unsigned x = (k[0] ^ k[i]) & P;  // exchange the low bits of axes 0 and i
+                k[0] ^= x;
+                k[i] ^= x;
+            }
+        }
+    }
+    k[1] ^= k[0];
+    k[2] ^= k[1];
+    unsigned g = 0;
+    for (unsigned Q = 128u; Q > 1u; Q >>= 1)
+        if (k[2] & Q) g ^= Q - 1u;
+    k[0] ^= g; k[1] ^= g; k[2] ^= g;
     unsigned code = 0;
     for (int b = 7; b >= 0; --b)
         code = (code << 3) | (((k[0] >> b) & 1u) << 2) | (((k[1] >> b) & 1u) << 1) | ((k[2] >> b) & 1u);
@@ -446,7 +468,7 @@ int check_query_args(const sd_tree* t, const float* q, int64_t M, const float* v
 
 namespace {
 
-// Morton order of the queries into `order` (stream-ordered scratch).
+// Hilbert order of the queries into `order` (stream-ordered scratch).
 int compute_order(const sd_tree* t, const float* q, int m, int32_t* order, cudaStream_t st)
 {
     size_t hw = sdsort::hist_words(m, 3);
@@ -570,7 +592,7 @@ extern "C" int sd_query_status(const sd_tree* t, void* stream)
 // fixed device-memory budget and forbids allocation during a simulation
 // step, where a cudaMalloc could block on the device or fail part-way).
 // Its temporary storage — the packet counter of the persistent traversal and
-// the buffers of the query Morton sort — lives in one file-scope device
+// the buffers of the query order sort — lives in one file-scope device
 // array of fixed size, so the call allocates nothing. Limits and sharing:
 //   * at most SD_NOALLOC_MAX_QUERIES queries per call;
 //   * every device that loads this library holds the array until the
@@ -661,7 +683,7 @@ size_t order_scratch_bytes(int m)
     return sizeof(unsigned) * 2 * (size_t)m + sizeof(int) * (size_t)m + sizeof(uint32_t) * sdsort::hist_words(m, 3) + 256;
 }
 
-// Morton order of m queries into `order`, using caller scratch of
+// Hilbert order of m queries into `order`, using caller scratch of
 // order_scratch_bytes(m) bytes (256-byte aligned).
 int order_into(const sd_tree* t, const float* q, int m, int32_t* order, void* scratch, cudaStream_t st)
 {

@@ -186,3 +186,25 @@ def test_degenerate_geometry_and_contact():
     assert_parity(_np(v), _np(g), rv, rg, 20.0, dmin, "degenerate")
     v, g = sd.query(_t(q))
     assert_parity(_np(v), _np(g), rv, rg, 20.0, dmin, "degenerate bh")
+
+
+def test_query_order_is_a_hilbert_walk():
+    """sd_query_order on the centres of an aligned 16^3 block of its 256^3
+    grid: a permutation in which consecutive queries are face neighbours
+    (the Hilbert curve covers every aligned block contiguously), and the
+    traversal result is independent of the order up to summation order."""
+    from paper_2108_10480_gb300 import SmoothDistance
+    P = np.array([[0.0, 0.0, 0.0], [256.0, 256.0, 256.0]], np.float32)
+    sd = SmoothDistance(points=P, alpha=1.0, beta=0.5, device="cuda:0")
+    g = np.stack(np.meshgrid(*[np.arange(32, 48)] * 3, indexing="ij"), -1).reshape(-1, 3)
+    rng = np.random.default_rng(0)
+    g = g[rng.permutation(len(g))]
+    q = torch.from_numpy((g + 0.5).astype(np.float32)).cuda()
+    order = sd.query_order(q).cpu().numpy()
+    assert np.array_equal(np.sort(order), np.arange(len(g)))
+    walk = g[order]
+    step = np.abs(np.diff(walk, axis=0))
+    assert np.all(step.sum(1) == 1)
+    v0, g0 = sd.query(q, sort=False)
+    v1, g1 = sd.query(q)
+    assert torch.allclose(v0, v1, rtol=1e-6) and torch.allclose(g0, g1, rtol=1e-5, atol=1e-7)
