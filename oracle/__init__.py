@@ -81,12 +81,26 @@ def _load():
         lib.orc_lower_bound.argtypes = [P, d, d, i, P, i64, P, P, P]
         lib.orc_lower_bound.restype = i
         lib.orc_prim_kappa.argtypes = [P, P]
+        lib.orc_simplex_closest.argtypes = [P, i, P, i, P, P]
+        lib.orc_simplex_closest.restype = d
+        lib.orc_brute_prims.argtypes = [P, d, d, i, i, P, P, i, i64, P, P, P, i]
+        lib.orc_bh_prims.argtypes = [P, d, d, d, i, i, i, P, P, i, i64, P, P, P, P, i]
+        lib.orc_bh_prims.restype = i
         _lib = lib
         return lib
 
 
 def _ptr(a):
     return ctypes.c_void_p(a.ctypes.data) if a is not None and a.size else ctypes.c_void_p(0)
+
+
+def simplex_closest(A, B):
+    """Distance and closest points of two simplices (1-3 vertices each)."""
+    A = np.ascontiguousarray(np.asarray(A, np.float64).reshape(-1, 3))
+    B = np.ascontiguousarray(np.asarray(B, np.float64).reshape(-1, 3))
+    pa = np.zeros(3); pb = np.zeros(3)
+    d = _load().orc_simplex_closest(_ptr(A), A.shape[0], _ptr(B), B.shape[0], _ptr(pa), _ptr(pb))
+    return d, pa, pb
 
 
 def default_threads() -> int:
@@ -214,6 +228,41 @@ class Scene:
                             int(threads or default_threads()))
         if rc != 0:
             raise RuntimeError("orc_bh failed")
+        return val, grad, counts, margin
+
+    # -- query primitives (Sec. 3.4) -------------------------------------
+    def brute_prims(self, QV, QF, alpha, alpha_u=0.0, paper_metric=False, unit=False, threads=None):
+        """Exact d^ and its translation gradient for query primitives QF [m, k]
+        (k = 1, 2, 3) over vertices QV [*, 3], and the exact minimum distance."""
+        V = np.ascontiguousarray(np.asarray(QV, np.float64).reshape(-1, 3))
+        F = np.ascontiguousarray(np.asarray(QF, np.int32))
+        F = F.reshape(F.shape[0], -1)
+        m, k = F.shape
+        val = np.zeros(m); grad = np.zeros((m, 3)); dmin = np.zeros(m)
+        _load().orc_brute_prims(self._h, float(alpha), float(alpha_u), int(bool(paper_metric)), int(bool(unit)),
+                                _ptr(V), _ptr(F), int(k), m, _ptr(val), _ptr(grad), _ptr(dmin),
+                                int(threads or default_threads()))
+        return val, grad, dmin
+
+    def bh_prims(self, QV, QF, alpha, beta, alpha_u=0.0, paper_metric=False, decision="fp32", threads=None,
+                 want_margin=False, unit=False):
+        """Barnes-Hut d^ for query primitives, the node test taken on the
+        query's box (see orc_bh_prims); returns (val, grad, counts, margin)."""
+        if self.L is None:
+            self.build_tree(1)
+        V = np.ascontiguousarray(np.asarray(QV, np.float64).reshape(-1, 3))
+        F = np.ascontiguousarray(np.asarray(QF, np.int32))
+        F = F.reshape(F.shape[0], -1)
+        m, k = F.shape
+        val = np.zeros(m); grad = np.zeros((m, 3)); counts = np.zeros((m, 3), np.int64)
+        margin = np.zeros(m) if want_margin else None
+        rc = _load().orc_bh_prims(self._h, float(alpha), float(alpha_u), float(beta), int(bool(paper_metric)),
+                                  int(bool(unit)), 0 if decision == "fp32" else 1, _ptr(V), _ptr(F), int(k), m,
+                                  _ptr(val), _ptr(grad), _ptr(counts),
+                                  _ptr(margin) if margin is not None else ctypes.c_void_p(0),
+                                  int(threads or default_threads()))
+        if rc != 0:
+            raise RuntimeError("orc_bh_prims failed")
         return val, grad, counts, margin
 
     def lower_bound(self, q, alpha, alpha_u=0.0, unit=False):

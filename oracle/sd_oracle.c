@@ -697,6 +697,169 @@ void orc_tree_export(void *h, uint64_t *codes, int64_t *sorted, int32_t *left, i
 }
 
 /* ------------------------------------------------------------------------ */
+/* query primitives (Sec. 3.4): an edge or a triangle as the query          */
+/* ------------------------------------------------------------------------ */
+/* Closest points of two simplices A (na vertices) and B (nb vertices): the
+   minimum of |A(lambda) - B(mu)|^2 over both barycentric simplices (the QP
+   of App. B). Every pair of faces (vertex subsets) is tried: the pair's
+   unconstrained minimiser on its affine hulls, kept if its barycentric
+   coordinates are feasible. The convex minimum lies in the relative interior
+   of some face pair, where it is that pair's unconstrained minimiser; a pair
+   whose normal equations are singular (parallel hulls) is skipped, since its
+   minimum is then also reached on a smaller face pair. The first face pair
+   in enumeration order that reaches the smallest distance gives pa, pb. */
+double orc_simplex_closest(const double *A, int na, const double *B, int nb, double *pa, double *pb)
+{
+    double best = INFINITY;
+    for (int sa = 1; sa < (1 << na); ++sa)
+        for (int sb = 1; sb < (1 << nb); ++sb) {
+            int ia[3], ib[3], ka = 0, kb = 0;
+            for (int i = 0; i < na; ++i) if ((sa >> i) & 1) ia[ka++] = i;
+            for (int j = 0; j < nb; ++j) if ((sb >> j) & 1) ib[kb++] = j;
+            const double *a0 = A + 3 * ia[0], *b0 = B + 3 * ib[0];
+            double M[3][4], r0[3];
+            int m = 0;
+            for (int i = 1; i < ka; ++i, ++m)
+                for (int j = 0; j < 3; ++j) M[j][m] = A[3 * ia[i] + j] - a0[j];
+            for (int i = 1; i < kb; ++i, ++m)
+                for (int j = 0; j < 3; ++j) M[j][m] = -(B[3 * ib[i] + j] - b0[j]);
+            for (int j = 0; j < 3; ++j) r0[j] = a0[j] - b0[j];
+            double z[4] = {0, 0, 0, 0};
+            if (m > 0) {
+                /* normal equations (M^T M) z = -M^T r0 by Gaussian elimination */
+                double G[4][5], scale = 0.0;
+                for (int p = 0; p < m; ++p) {
+                    for (int q = 0; q < m; ++q) {
+                        double g = 0.0;
+                        for (int j = 0; j < 3; ++j) g += M[j][p] * M[j][q];
+                        G[p][q] = g;
+                    }
+                    double rhs = 0.0;
+                    for (int j = 0; j < 3; ++j) rhs -= M[j][p] * r0[j];
+                    G[p][m] = rhs;
+                    if (G[p][p] > scale) scale = G[p][p];
+                }
+                int singular = scale <= 0.0;
+                for (int col = 0; col < m && !singular; ++col) {
+                    int piv = col;
+                    for (int r = col + 1; r < m; ++r) if (fabs(G[r][col]) > fabs(G[piv][col])) piv = r;
+                    if (fabs(G[piv][col]) <= 1e-13 * scale) { singular = 1; break; }
+                    if (piv != col)
+                        for (int q = 0; q <= m; ++q) { double t = G[col][q]; G[col][q] = G[piv][q]; G[piv][q] = t; }
+                    for (int r = 0; r < m; ++r) {
+                        if (r == col) continue;
+                        double f = G[r][col] / G[col][col];
+                        for (int q = col; q <= m; ++q) G[r][q] -= f * G[col][q];
+                    }
+                }
+                if (singular) continue;
+                for (int p = 0; p < m; ++p) z[p] = G[p][m] / G[p][p];
+            }
+            /* feasibility: barycentric coordinates of both points >= 0 */
+            double la0 = 1.0, mb0 = 1.0;
+            int ok = 1;
+            for (int i = 0; i < ka - 1; ++i) { ok &= z[i] >= 0.0; la0 -= z[i]; }
+            for (int i = 0; i < kb - 1; ++i) { ok &= z[ka - 1 + i] >= 0.0; mb0 -= z[ka - 1 + i]; }
+            if (!ok || la0 < 0.0 || mb0 < 0.0) continue;
+            double xa[3], xb[3];
+            for (int j = 0; j < 3; ++j) {
+                xa[j] = a0[j];
+                xb[j] = b0[j];
+                for (int i = 1; i < ka; ++i) xa[j] += z[i - 1] * (A[3 * ia[i] + j] - a0[j]);
+                for (int i = 1; i < kb; ++i) xb[j] += z[ka - 1 + i - 1] * (B[3 * ib[i] + j] - b0[j]);
+            }
+            double d2 = 0.0;
+            for (int j = 0; j < 3; ++j) d2 += (xa[j] - xb[j]) * (xa[j] - xb[j]);
+            if (d2 < best) {
+                best = d2;
+                for (int j = 0; j < 3; ++j) { pa[j] = xa[j]; pb[j] = xb[j]; }
+            }
+        }
+    return sqrt(best);
+}
+
+/* A query: its vertices (k = 1: a point) and its axis-aligned box. */
+typedef struct { double v[9]; int k; double lo[3], hi[3]; } query_t;
+
+static void query_point(query_t *Q, const double *q)
+{
+    Q->k = 1;
+    for (int j = 0; j < 3; ++j) Q->v[j] = Q->lo[j] = Q->hi[j] = q[j];
+}
+
+static void query_prim(query_t *Q, const double *V, const int32_t *f, int k)
+{
+    Q->k = k;
+    for (int j = 0; j < 3; ++j) { Q->lo[j] = INFINITY; Q->hi[j] = -INFINITY; }
+    for (int i = 0; i < k; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double x = V[3 * (int64_t)f[i] + j];
+            Q->v[3 * i + j] = x;
+            if (x < Q->lo[j]) Q->lo[j] = x;
+            if (x > Q->hi[j]) Q->hi[j] = x;
+        }
+}
+
+/* The exact term of data primitive p for query Q. For an edge or triangle
+   query the term is the point term at g's point of a closest pair (Sec. 3.4
+   takes the closest point on g wherever a single point is needed, as in the
+   weights); its distance is the simplex distance and its gradient is that of
+   a rigid translation of g. */
+static term_t query_term(const scene_t *s, const prim_t *p, const query_t *Q, const params_t *pr, double *dist)
+{
+    if (Q->k == 1) {
+        near_t nr;
+        term_t T = prim_term(s, p, Q->v, pr, &nr, NULL, NULL);
+        if (dist) *dist = nr.d;
+        return T;
+    }
+    int nv = p->kind == K_POINT ? 1 : (p->kind == K_SEG ? 2 : 3);
+    double F[9], pf[3], pg[3];
+    for (int i = 0; i < nv; ++i)
+        for (int j = 0; j < 3; ++j) F[3 * i + j] = s->V[3 * p->v[i] + j];
+    double d = orc_simplex_closest(F, nv, Q->v, Q->k, pf, pg);
+    if (dist) *dist = d;
+    return prim_term(s, p, pg, pr, NULL, NULL, NULL);
+}
+
+typedef struct {
+    const scene_t *s;
+    params_t pr;
+    const double *V;
+    const int32_t *QF;
+    int k;
+    double *val, *grad, *dmin;
+} qbrute_ctx;
+
+static void qbrute_one(void *c_, int64_t i, void *scratch)
+{
+    qbrute_ctx *c = (qbrute_ctx *)c_;
+    const scene_t *s = c->s;
+    term_t *T = (term_t *)scratch;
+    query_t Q;
+    query_prim(&Q, c->V, c->QF + (int64_t)c->k * i, c->k);
+    double dm = INFINITY;
+    for (int64_t n = 0; n < s->n; ++n) {
+        double d;
+        T[n] = query_term(s, &s->P[n], &Q, &c->pr, &d);
+        if (d < dm) dm = d;
+    }
+    lse_finish(T, s->n, c->pr.alpha, &c->val[i], &c->grad[3 * i]);
+    if (c->dmin) c->dmin[i] = dm;
+}
+
+/* Eq. 3 / Eq. 4 with query primitives: m primitives of k vertices each
+   (QF [m, k] indices into V [*, 3]); grad is that of a rigid translation. */
+void orc_brute_prims(void *h, double alpha, double alpha_u, int paper_metric, int unit, const double *V,
+                     const int32_t *QF, int k, int64_t m, double *val, double *grad, double *dmin, int nthreads)
+{
+    scene_t *s = (scene_t *)h;
+    qbrute_ctx c = {s, {alpha, alpha / (alpha > alpha_u ? alpha : alpha_u), paper_metric, unit}, V, QF, k, val,
+                    grad, dmin};
+    run_pool(qbrute_one, &c, m, sizeof(term_t) * (size_t)(s->n ? s->n : 1), nthreads);
+}
+
+/* ------------------------------------------------------------------------ */
 /* Barnes-Hut (Alg. 1 / Alg. 2, App. D)                                     */
 /* ------------------------------------------------------------------------ */
 typedef struct {
@@ -706,7 +869,9 @@ typedef struct {
     float beta2f;
     int decision;          /* 0: fp32 squared test, 1: fp64 ratio test */
     double wfar;           /* max(A_E, A_T)^S */
-    const double *q;
+    const double *q;       /* query points [m,3], or the query mesh's vertices */
+    const int32_t *QF;     /* query primitives [m, qk] (NULL: point queries) */
+    int qk;
     double *val, *grad;
     int64_t *counts;       /* [m, 3]: nodes tested, far-field accepts, leaf primitives */
     double *margin;        /* min over tested nodes of |ratio - beta| / beta */
@@ -723,18 +888,25 @@ static void acc_push(acc_t *a, term_t t)
     a->T[a->n++] = t;
 }
 
-/* The Barnes-Hut condition |B| / d(y_B, q) < beta with y_B the closest point
-   of the box (Sec. 3.5, App. D). Decision mode 0 takes it in FP32 as
-   diag^2 < beta^2 * dbox^2 with the operation order fixed below (squares
-   summed as fma(z, z, fma(y, y, x * x)), each fma rounded once); mode 1 in
-   FP64 as the ratio. A query inside the box (d = 0) always opens it. */
-static int bh_condition(const bh_ctx *c, const float *lo, const float *hi, const double *q, double *margin)
+/* The Barnes-Hut condition |B| / d(y_B, g) < beta with y_B the closest point
+   of the box (Sec. 3.5, App. D). The query g is given by its axis-aligned
+   box [qlo, qhi] (a point: qlo = qhi = q). For an edge or triangle query the
+   halfspace test of Sec. 3.5 is taken on that box: the box halfspaces that g
+   lies entirely outside of are those where g's box is beyond the node's, and
+   the distance to the feature they identify is replaced by the distance
+   between the two boxes, a lower bound of it (equal to it for one halfspace
+   and for points), so the far field stays an underestimate. Decision mode 0
+   takes the test in FP32 as diag^2 < beta^2 * dbox^2 with the operation
+   order fixed below (squares summed as fma(z, z, fma(y, y, x * x)), each fma
+   rounded once); mode 1 in FP64 as the ratio. Overlapping boxes (d = 0)
+   always open the node. */
+static int bh_condition(const bh_ctx *c, const float *lo, const float *hi, const double *qlo, const double *qhi,
+                        double *margin)
 {
     if (c->decision == 0) {
-        float qf[3] = {(float)q[0], (float)q[1], (float)q[2]};
         float dx[3], ex[3];
         for (int j = 0; j < 3; ++j) {
-            float a = lo[j] - qf[j], b = qf[j] - hi[j];
+            float a = lo[j] - (float)qhi[j], b = (float)qlo[j] - hi[j];
             float m = a > b ? a : b;
             dx[j] = m > 0.0f ? m : 0.0f;
             ex[j] = hi[j] - lo[j];
@@ -754,8 +926,8 @@ static int bh_condition(const bh_ctx *c, const float *lo, const float *hi, const
         double d2 = 0.0, g2 = 0.0;
         for (int j = 0; j < 3; ++j) {
             double l = lo[j], h = hi[j];
-            double y = q[j] < l ? l : (q[j] > h ? h : q[j]);
-            d2 += (q[j] - y) * (q[j] - y);
+            double gap = qhi[j] < l ? l - qhi[j] : (qlo[j] > h ? qlo[j] - h : 0.0);
+            d2 += gap * gap;
             g2 += (h - l) * (h - l);
         }
         if (d2 <= 0.0) return 0;
@@ -768,14 +940,15 @@ static int bh_condition(const bh_ctx *c, const float *lo, const float *hi, const
     }
 }
 
+/* far-field term at the node box's nearest point to the query box: the
+   offset is g's box minus the node's per axis (0 where they overlap) */
 static void far_term(const bh_ctx *c, const float *lo, const float *hi, int64_t nB, int pts_only,
-                     const double *q, acc_t *a)
+                     const double *qlo, const double *qhi, acc_t *a)
 {
-    double y[3], dv[3];
+    double dv[3];
     for (int j = 0; j < 3; ++j) {
         double l = lo[j], h = hi[j];
-        y[j] = q[j] < l ? l : (q[j] > h ? h : q[j]);
-        dv[j] = q[j] - y[j];
+        dv[j] = qhi[j] < l ? qhi[j] - l : (qlo[j] > h ? qlo[j] - h : 0.0);
     }
     double d = sqrt(dot3(dv, dv));
     double wB = pts_only ? 1.0 : c->wfar;
@@ -786,31 +959,32 @@ static void far_term(const bh_ctx *c, const float *lo, const float *hi, int64_t 
 }
 
 /* Alg. 1, recursive: the Barnes-Hut test first (also at leaves), else exact
-   leaf terms, else both children. */
-static void collect(const bh_ctx *c, int32_t node, int is_leaf, const double *q, acc_t *a)
+   leaf terms, else both children. Q: the query (a point, or a primitive of
+   Q->k vertices) and its box. */
+static void collect(const bh_ctx *c, int32_t node, int is_leaf, const query_t *Q, acc_t *a)
 {
     const scene_t *s = c->s;
     const float *lo, *hi; int64_t nB; int po;
     if (is_leaf) { lo = s->llo[node]; hi = s->lhi[node]; nB = s->lcount[node]; po = s->lpts_only[node]; }
     else { lo = s->nlo[node]; hi = s->nhi[node]; nB = s->ncount[node]; po = s->npts_only[node]; }
     a->tested++;
-    if (bh_condition(c, lo, hi, q, c->margin ? &a->margin : NULL)) {
+    if (bh_condition(c, lo, hi, Q->lo, Q->hi, c->margin ? &a->margin : NULL)) {
         a->far++;
-        far_term(c, lo, hi, nB, po, q, a);
+        far_term(c, lo, hi, nB, po, Q->lo, Q->hi, a);
         return;
     }
     if (is_leaf) {
         int64_t e = ((int64_t)node + 1) * s->L < s->n ? ((int64_t)node + 1) * s->L : s->n;
         for (int64_t k = (int64_t)node * s->L; k < e; ++k) {
-            acc_push(a, prim_term(s, &s->P[s->sorted[k]], q, &c->pr, NULL, NULL, NULL));
+            acc_push(a, query_term(s, &s->P[s->sorted[k]], Q, &c->pr, NULL));
             a->leafp++;
         }
         return;
     }
     int32_t ch[2] = {s->left[node], s->right[node]};
     for (int k = 0; k < 2; ++k) {
-        if (ch[k] < 0) collect(c, -ch[k] - 1, 1, q, a);
-        else collect(c, ch[k], 0, q, a);
+        if (ch[k] < 0) collect(c, -ch[k] - 1, 1, Q, a);
+        else collect(c, ch[k], 0, Q, a);
     }
 }
 
@@ -819,9 +993,11 @@ static void bh_one(void *c_, int64_t i, void *scratch)
     bh_ctx *c = (bh_ctx *)c_;
     acc_t *a = (acc_t *)scratch;
     a->n = 0; a->tested = a->far = a->leafp = 0; a->margin = INFINITY;
-    const double *q = c->q + 3 * i;
-    if (c->s->nb == 1) collect(c, 0, 1, q, a);
-    else if (c->s->nb > 1) collect(c, 0, 0, q, a);
+    query_t Q;
+    if (c->QF) query_prim(&Q, c->q, c->QF + (int64_t)c->qk * i, c->qk);
+    else query_point(&Q, c->q + 3 * i);
+    if (c->s->nb == 1) collect(c, 0, 1, &Q, a);
+    else if (c->s->nb > 1) collect(c, 0, 0, &Q, a);
     lse_finish(a->T, a->n, c->pr.alpha, &c->val[i], &c->grad[3 * i]);
     if (c->counts) { c->counts[3 * i] = a->tested; c->counts[3 * i + 1] = a->far; c->counts[3 * i + 2] = a->leafp; }
     if (c->margin) c->margin[i] = a->margin;
@@ -845,8 +1021,11 @@ static void *bh_worker(void *arg)
     return NULL;
 }
 
-int orc_bh(void *h, double alpha, double alpha_u, double beta, int paper_metric, int unit, int decision,
-           const double *q, int64_t m, double *val, double *grad, int64_t *counts, double *margin, int nthreads)
+/* Barnes-Hut over m queries: points q [m,3] (qf_prims NULL) or primitives
+   qf_prims [m, qk_prims] indexing the vertex array q. */
+static int bh_run(void *h, double alpha, double alpha_u, double beta, int paper_metric, int unit, int decision,
+                  const double *q, const int32_t *qf_prims, int qk_prims, int64_t m, double *val, double *grad,
+                  int64_t *counts, double *margin, int nthreads)
 {
     scene_t *s = (scene_t *)h;
     if (s->n > 0 && s->nb == 0) return -1;
@@ -863,6 +1042,7 @@ int orc_bh(void *h, double alpha, double alpha_u, double beta, int paper_metric,
     double A = s->A_E > s->A_T ? s->A_E : s->A_T;
     c.wfar = unit ? 1.0 : pow(A, c.pr.S);
     c.q = q; c.val = val; c.grad = grad; c.counts = counts; c.margin = margin;
+    c.QF = qf_prims; c.qk = qk_prims;
     bh_pool_t p; p.c = &c; p.m = m; p.next = 0;
     pthread_mutex_init(&p.mu, NULL);
     if (nthreads < 1) nthreads = 1;
@@ -872,6 +1052,21 @@ int orc_bh(void *h, double alpha, double alpha_u, double beta, int paper_metric,
     free(th);
     pthread_mutex_destroy(&p.mu);
     return 0;
+}
+
+int orc_bh(void *h, double alpha, double alpha_u, double beta, int paper_metric, int unit, int decision,
+           const double *q, int64_t m, double *val, double *grad, int64_t *counts, double *margin, int nthreads)
+{
+    return bh_run(h, alpha, alpha_u, beta, paper_metric, unit, decision, q, NULL, 1, m, val, grad, counts, margin,
+                  nthreads);
+}
+
+int orc_bh_prims(void *h, double alpha, double alpha_u, double beta, int paper_metric, int unit, int decision,
+                 const double *V, const int32_t *QF, int k, int64_t m, double *val, double *grad, int64_t *counts,
+                 double *margin, int nthreads)
+{
+    return bh_run(h, alpha, alpha_u, beta, paper_metric, unit, decision, V, QF, k, m, val, grad, counts, margin,
+                  nthreads);
 }
 
 /* ------------------------------------------------------------------------ */
