@@ -262,6 +262,43 @@ int sd_lower_bound(const sd_tree* t, const float* q, int64_t M, float margin, fl
 int sd_surrogate_query(const sd_tree* t, const float* params, const float* frame, float margin, const float* q,
                        int64_t M, float* value, float* grad, int32_t* routed, int64_t* n_routed, void* stream);
 
+/*
+ * Edge and triangle queries (Sec. 3.4): the smooth distance of Eq. 3 from
+ * each of M query primitives g_j to the data mesh, with the simplex-simplex
+ * distance of App. B, the weights taken at g_j's point of a closest pair,
+ * and the Barnes-Hut test of Sec. 3.5 on g_j's axis-aligned box (the box
+ * halfspaces g_j lies entirely outside of; the distance to the feature they
+ * identify lower-bounded by the gap between the boxes).
+ *   QV     device [nqv,3] float32 query-mesh vertices
+ *   QF     device [M,k] int32 vertex indices; k = 1 (points), 2 (edges) or
+ *          3 (triangles)
+ *   value  device [M] d^(g_j); grad device [M,3] (may be NULL) its gradient
+ *          for a rigid translation of g_j
+ *   opts   as for sd_query (sort_queries orders by the Hilbert index of each
+ *          primitive's centroid; order, block, counts as for sd_query)
+ * A primitive with an index outside [0, nqv) or a non-finite vertex gets NaN
+ * outputs and sets the status word (SD_ERR_INDEX / SD_ERR_NONFINITE).
+ * Asynchronous; uses stream-ordered temporary memory.
+ */
+int sd_query_prims(const sd_tree* t, const float* QV, int64_t nqv, const int32_t* QF, int32_t k, int64_t M,
+                   float* value, float* grad, const sd_query_opts* opts, void* stream);
+
+/*
+ * Smooth distance between the data mesh and a query mesh (Sec. 3.6,
+ * Eq. lse_full) from sd_query_prims' outputs, and its gradient per query
+ * vertex (Eq. lse_full2 / Eq. dlse_full: each primitive's softmin share
+ * split equally between its k vertices):
+ *   out    device [1]: D = -(1/alpha_q) log sum_j exp(-alpha_q d^_j)
+ *   vgrad  device [nqv,3] (may be NULL): dD/dv_k; vertices used by no
+ *          primitive get 0; indices outside [0, nqv) are ignored
+ *   status device int (may be NULL): SD_ERR_TIMEOUT's bit is or-ed in if a
+ *          bounded wait of the vertex sort ran out
+ * Sums run in a fixed order (deterministic). Asynchronous; uses
+ * stream-ordered temporary memory.
+ */
+int sd_mesh_reduce(const int32_t* QF, int32_t k, int64_t M, int64_t nqv, const float* value, const float* grad,
+                   float alpha_q, float* out, float* vgrad, int32_t* status, void* stream);
+
 /* Synchronise `stream`, return and clear the tree's device status word. */
 int sd_query_status(const sd_tree* t, void* stream);
 

@@ -819,7 +819,38 @@ static term_t query_term(const scene_t *s, const prim_t *p, const query_t *Q, co
         for (int j = 0; j < 3; ++j) F[3 * i + j] = s->V[3 * p->v[i] + j];
     double d = orc_simplex_closest(F, nv, Q->v, Q->k, pf, pg);
     if (dist) *dist = d;
-    return prim_term(s, p, pg, pr, NULL, NULL, NULL);
+    double scale = 1.0;
+    for (int j = 0; j < 3; ++j) scale = fmax(scale, fabs(pg[j]));
+    const double tol = 1e-12 * scale;
+    if (d <= tol && nv == 3 && Q->k == 3) {
+        /* crossing triangles touch along a segment: the point taken is the
+           mean of the points where an edge of one pierces the other (the
+           segment's midpoint in general position) */
+        double sum[3] = {0, 0, 0};
+        int hits = 0;
+        for (int side = 0; side < 2; ++side)
+            for (int e = 0; e < 3; ++e) {
+                const double *T3 = side ? F : Q->v, *O3 = side ? Q->v : F;
+                double E[6], a[3], b[3];
+                for (int j = 0; j < 3; ++j) { E[j] = O3[3 * e + j]; E[3 + j] = O3[3 * ((e + 1) % 3) + j]; }
+                if (orc_simplex_closest(E, 2, T3, 3, a, b) <= tol) {
+                    for (int j = 0; j < 3; ++j) sum[j] += a[j];
+                    ++hits;
+                }
+            }
+        if (hits)
+            for (int j = 0; j < 3; ++j) pg[j] = sum[j] / hits;
+    }
+    near_t nr;
+    term_t T = prim_term(s, p, pg, pr, &nr, NULL, NULL);
+    /* touching primitives: the point term at the touching point has a
+       distance at rounding level with a meaningless direction; the pair's
+       distance is 0 and, as for d = 0 in Eq. dgrad, its gradient is 0 */
+    if (d <= tol) {
+        T.t += pr->alpha * nr.d;
+        for (int j = 0; j < 3; ++j) T.v[j] -= nr.gd[j];
+    }
+    return T;
 }
 
 typedef struct {

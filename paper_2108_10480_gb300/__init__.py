@@ -24,6 +24,19 @@ def lib():
     return _native.lib()
 
 
+def mesh_reduce(F, nverts, value, grad, alpha_q, stream=None):
+    """Smooth distance to a query mesh and its per-vertex gradient
+    (sd_mesh_reduce) from query_prims' outputs: (D [1], vgrad [nverts, 3])."""
+    F = F.to(torch.int32).contiguous()
+    m, k = F.shape
+    out = torch.empty(1, device=F.device)
+    vg = torch.empty(int(nverts), 3, device=F.device)
+    rc = lib().sd_mesh_reduce(_ptr(F), int(k), m, int(nverts), _ptr(value), _ptr(grad), float(alpha_q), _ptr(out),
+                              _ptr(vg), None, _stream_handle(stream))
+    _native.check(rc, "sd_mesh_reduce")
+    return out, vg
+
+
 def kernel_launches() -> int:
     """CUDA kernels libsd has launched in this process."""
     return int(lib().sd_kernel_launches())
@@ -157,6 +170,28 @@ class SmoothDistance:
     def query_brute(self, q, grad=True, stream=None, out=None):
         """Plain all-pairs d^ and grad d^ (sd_query_brute)."""
         return self._run(lib().sd_query_brute, q, grad, False, False, 0, stream, out)
+
+    def query_prims(self, V, F, sort=True, counts=False, block=0, stream=None, out=None, order=None):
+        """Smooth distance of edge (F [m,2]) or triangle (F [m,3]) queries over
+        vertices V [n,3] (sd_query_prims): value [m] and the gradient [m,3]
+        for a rigid translation of each primitive (plus work counts)."""
+        V = _dev_f32(V, self.device)
+        F = torch.as_tensor(F).to(device=self.device, dtype=torch.int32)
+        F = F.reshape(F.shape[0], -1).contiguous()
+        m, k = F.shape
+        val, grad = out if out is not None else (torch.empty(m, device=self.device),
+                                                 torch.empty(m, 3, device=self.device))
+        cnt = torch.empty(m, 3, dtype=torch.int32, device=self.device) if counts else None
+        o = _native.SdQueryOpts()
+        lib().sd_default_query_opts(ctypes.byref(o))
+        o.sort_queries = 1 if sort else 0
+        o.block = int(block)
+        o.counts = _ptr(cnt)
+        o.order = _ptr(order)
+        rc = lib().sd_query_prims(self._h, _ptr(V), V.shape[0], _ptr(F), int(k), m, _ptr(val), _ptr(grad),
+                                  ctypes.byref(o), _stream_handle(stream))
+        _native.check(rc, "sd_query_prims")
+        return (val, grad, cnt) if counts else (val, grad)
 
     def status(self, stream=None) -> int:
         """Synchronise and return (then clear) the device status word."""

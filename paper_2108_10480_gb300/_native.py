@@ -85,6 +85,10 @@ SIGNATURES = {
     "sd_mlp_train_step": (ctypes.c_int, [c_void_p, c_void_p, c_void_p, c_int32, c_float, c_void_p, c_void_p,
                                          c_void_p, c_int64, c_void_p, c_void_p, c_void_p, ctypes.c_size_t,
                                          c_void_p]),
+    "sd_query_prims": (ctypes.c_int, [c_void_p, c_void_p, c_int64, c_void_p, ctypes.c_int32, c_int64, c_void_p,
+                                      c_void_p, ctypes.POINTER(SdQueryOpts), c_void_p]),
+    "sd_mesh_reduce": (ctypes.c_int, [c_void_p, ctypes.c_int32, c_int64, c_int64, c_void_p, c_void_p, c_float,
+                                      c_void_p, c_void_p, c_void_p, c_void_p]),
     "sd_lower_bound": (ctypes.c_int, [c_void_p, c_void_p, c_int64, c_float, c_void_p, c_void_p, c_void_p, c_void_p]),
     "sd_surrogate_query": (ctypes.c_int, [c_void_p, c_void_p, c_void_p, c_float, c_void_p, c_int64, c_void_p,
                                           c_void_p, c_void_p, ctypes.POINTER(c_int64), c_void_p]),

@@ -145,6 +145,7 @@ __device__ __forceinline__ float sd_dop(float a, float b, float c, float d)
 
 __device__ __forceinline__ float3 f3(float x, float y, float z) { return make_float3(x, y, z); }
 __device__ __forceinline__ float3 sub(float3 a, float3 b) { return f3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ __forceinline__ float3 add(float3 a, float3 b) { return f3(a.x + b.x, a.y + b.y, a.z + b.z); }
 __device__ __forceinline__ float dot(float3 a, float3 b) { return fmaf(a.x, b.x, fmaf(a.y, b.y, a.z * b.z)); }
 __device__ __forceinline__ float3 scale(float3 a, float s) { return f3(a.x * s, a.y * s, a.z * s); }
 __device__ __forceinline__ float3 axpy(float s, float3 x, float3 y) { return f3(fmaf(s, x.x, y.x), fmaf(s, x.y, y.y), fmaf(s, x.z, y.z)); }
@@ -306,15 +307,20 @@ __device__ __forceinline__ float tri_weight(const SdParams& P, float p1, float p
 // exponent y, the multiplicative weight w and the gradient vector v so that
 // the term is w 2^y with gradient numerator w 2^y v (Eq. 4).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void leaf_point(const SdParams& P, float3 q, float4 h, float& y, float& w, float3& v)
+// (The *_rel forms take the query relative to the primitive's first vertex.)
+__device__ __forceinline__ void leaf_point_rel(const SdParams& P, float3 d, float& y, float& w, float3& v)
 {
-    float3 d = sub(q, f3(h.x, h.y, h.z));
     float d2 = dot(d, d);
     float dist = sqrtf(d2);
     float inv = dist > 0.f ? 1.f / dist : 0.f;
     y = -P.alpha2 * dist;
     w = 1.f;
     v = scale(d, inv);
+}
+
+__device__ __forceinline__ void leaf_point(const SdParams& P, float3 q, float4 h, float& y, float& w, float3& v)
+{
+    leaf_point_rel(P, sub(q, f3(h.x, h.y, h.z)), y, w, v);
 }
 
 // weight factor for a weighted primitive: w~ and grad w~ -> (y, w, v)
@@ -342,19 +348,17 @@ __device__ __forceinline__ void apply_weight(const SdParams& P, float A, float d
 }
 
 template <bool GRAD>
-__device__ __forceinline__ void leaf_segment(const SdParams& P, float3 q, float4 h, float4 x0, float4 x1,
-                                             float& y, float& w, float3& v)
+__device__ __forceinline__ void leaf_segment_rel(const SdParams& P, float3 ap, float4 x0, float4 x1,
+                                                 float& y, float& w, float3& v, bool touch = false)
 {
-    float3 a = f3(h.x, h.y, h.z);
     float3 e = f3(x0.x, x0.y, x0.z);
     float u = x0.w, vv = x1.x;
-    float3 ap = sub(q, a);
     float ee = dot(e, e);
     float t = ee > 0.f ? dot(ap, e) / ee : 0.f;
     bool inside = t > 0.f && t < 1.f;
     t = fminf(fmaxf(t, 0.f), 1.f);
     float3 diff = axpy(-t, e, ap);
-    float dist = sqrtf(dot(diff, diff));
+    float dist = touch ? 0.f : sqrtf(dot(diff, diff));   // touch: a query primitive touching it
     float3 gd = scale(diff, dist > 0.f ? 1.f / dist : 0.f);
     float dw = 0.f;
     float wt = (u == 1.f && vv == 1.f) ? 1.f : edge_weight(t, u, vv, dw);
@@ -363,13 +367,19 @@ __device__ __forceinline__ void leaf_segment(const SdParams& P, float3 q, float4
     apply_weight<GRAD>(P, __ldg(&P.sc->A_E), dist, wt, gwt, gd, y, w, v);
 }
 
+template <bool GRAD>
+__device__ __forceinline__ void leaf_segment(const SdParams& P, float3 q, float4 h, float4 x0, float4 x1,
+                                             float& y, float& w, float3& v)
+{
+    leaf_segment_rel<GRAD>(P, sub(q, f3(h.x, h.y, h.z)), x0, x1, y, w, v);
+}
+
 // Closest point of a triangle by its Voronoi regions (vertex, edge, face),
 // in coordinates relative to v0; differences of products use sd_dop.
 template <bool GRAD>
-__device__ __forceinline__ void leaf_triangle(const SdParams& P, float3 q, float4 h, float4 x0, float4 x1,
-                                              float& y, float& w, float3& v)
+__device__ __forceinline__ void leaf_triangle_rel(const SdParams& P, float3 ap, float4 x0, float4 x1,
+                                                  float& y, float& w, float3& v, bool touch = false)
 {
-    float3 ap = sub(q, f3(h.x, h.y, h.z));
     float3 e1 = f3(x0.x, x0.y, x0.z);
     float3 e2 = f3(x1.x, x1.y, x1.z);
     float iv = x0.w, ie = x1.w;
@@ -437,7 +447,7 @@ __device__ __forceinline__ void leaf_triangle(const SdParams& P, float3 q, float
         }
         gp1 = gp2 = f3(0.f, 0.f, 0.f);
     }
-    float dist = sqrtf(dot(diff, diff));
+    float dist = touch ? 0.f : sqrtf(dot(diff, diff));   // touch: a query primitive touching it
     float3 gd = scale(diff, dist > 0.f ? 1.f / dist : 0.f);
     float wt = 1.f;
     float3 gwt = f3(0.f, 0.f, 0.f);
@@ -448,6 +458,13 @@ __device__ __forceinline__ void leaf_triangle(const SdParams& P, float3 q, float
         if (wt < 1e-6f) gwt = f3(0.f, 0.f, 0.f);
     }
     apply_weight<GRAD>(P, __ldg(&P.sc->A_T), dist, wt, gwt, gd, y, w, v);
+}
+
+template <bool GRAD>
+__device__ __forceinline__ void leaf_triangle(const SdParams& P, float3 q, float4 h, float4 x0, float4 x1,
+                                              float& y, float& w, float3& v)
+{
+    leaf_triangle_rel<GRAD>(P, sub(q, f3(h.x, h.y, h.z)), x0, x1, y, w, v);
 }
 
 // one primitive at sorted position k

@@ -15,6 +15,7 @@
 #include <mutex>
 
 #include "sd_common.cuh"
+#include "sd_pairs.cuh"
 #include "sd_sort.cuh"
 
 namespace {
@@ -34,6 +35,25 @@ constexpr int PK_QCAP = 64;       // leaf queue: < 32 pending + at most 32 pushe
 constexpr int PK_MAX_THREADS = 256;
 constexpr int PK_WARP_INTS = 2 * PK_STACK + 2 * PK_QCAP + 32;   // per-warp shared memory, in ints
 
+// Query primitives (Sec. 3.4): QK vertices each, indices F [m, QK] into the
+// vertex array V [nv, 3] (unused for point queries, QK = 1).
+struct QPrims {
+    const float* V;
+    const int* F;
+    int nv;
+};
+
+// the vertices of query primitive qi (indices already validated)
+template <int QK>
+__device__ __forceinline__ void load_prim(const QPrims& Q, int qi, float3 (&g)[QK])
+{
+#pragma unroll
+    for (int c = 0; c < QK; ++c) {
+        int vi = __ldg(&Q.F[QK * qi + c]);
+        g[c] = f3(__ldg(&Q.V[3 * vi]), __ldg(&Q.V[3 * vi + 1]), __ldg(&Q.V[3 * vi + 2]));
+    }
+}
+
 struct WarpShared {
     int2* stack;
     int2* queue;
@@ -42,21 +62,32 @@ struct WarpShared {
 
 // Evaluate n <= 32 queued (owner lane, primitive) pairs, one per lane, and
 // fold each result into its owner's accumulator.
-template <int KINDS, bool GRAD>
-__device__ __forceinline__ void flush_queue(const SdParams& P, float3 q, const int2* items, int n, const WarpShared& ws,
-                                            int lane, Lse& acc)
+template <int KINDS, bool GRAD, int QK>
+__device__ __forceinline__ void flush_queue(const SdParams& P, float3 q, int qi, const QPrims& QP, const int2* items,
+                                            int n, const WarpShared& ws, int lane, Lse& acc)
 {
     __syncwarp();
     bool has = lane < n;
     int2 it = has ? items[lane] : make_int2(lane, 0);
     int owner = it.x;
-    float3 qo = f3(__shfl_sync(0xffffffffu, q.x, owner), __shfl_sync(0xffffffffu, q.y, owner),
-                   __shfl_sync(0xffffffffu, q.z, owner));
+    float3 qo = q;
+    int qio = 0;
+    if (QK == 1)
+        qo = f3(__shfl_sync(0xffffffffu, q.x, owner), __shfl_sync(0xffffffffu, q.y, owner),
+                __shfl_sync(0xffffffffu, q.z, owner));
+    else
+        qio = __shfl_sync(0xffffffffu, qi, owner);
     float tm = -INFINITY, ts = 0.f, tx = 0.f, ty = 0.f, tz = 0.f;
     if (has) {
         float y, w;
         float3 v;
-        leaf_term<KINDS, GRAD>(P, qo, it.y, y, w, v);
+        if constexpr (QK == 1) {
+            leaf_term<KINDS, GRAD>(P, qo, it.y, y, w, v);
+        } else {
+            float3 g[QK];
+            load_prim<QK>(QP, qio, g);
+            leaf_term_q<KINDS, GRAD, QK>(P, g, it.y, y, w, v);
+        }
         tm = y; ts = w;
         if (GRAD) { tx = w * v.x; ty = w * v.y; tz = w * v.z; }
     }
@@ -100,9 +131,9 @@ __device__ __forceinline__ void flush_queue(const SdParams& P, float3 q, const i
 }
 
 // queue the leaf bucket `ref` for the lanes in `lm`, flushing full groups of 32
-template <int KINDS, bool GRAD>
-__device__ __forceinline__ void queue_leaf(const SdParams& P, float3 q, bool leaf, unsigned lm, int ref, Lse& acc,
-                                           const WarpShared& ws, int& nq, int lane, int& nleaf)
+template <int KINDS, bool GRAD, int QK>
+__device__ __forceinline__ void queue_leaf(const SdParams& P, float3 q, int qi, const QPrims& QP, bool leaf, unsigned lm,
+                                           int ref, Lse& acc, const WarpShared& ws, int& nq, int lane, int& nleaf)
 {
     int k0 = (-ref - 1) * P.L;
     int k1 = min(k0 + P.L, P.n_prims);
@@ -114,7 +145,7 @@ __device__ __forceinline__ void queue_leaf(const SdParams& P, float3 q, bool lea
         nq += cnt;
         if (nq >= 32) {
             nq -= 32;
-            flush_queue<KINDS, GRAD>(P, q, ws.queue + nq, 32, ws, lane, acc);
+            flush_queue<KINDS, GRAD, QK>(P, q, qi, QP, ws.queue + nq, 32, ws, lane, acc);
         }
     }
 }
@@ -125,10 +156,11 @@ __device__ __forceinline__ void queue_leaf(const SdParams& P, float3 q, bool lea
 // both far-field terms of App. D (n_B w_B e^{-alpha d} with direction
 // (q - y_B)/d) are added without branches. Returns the lane masks of the
 // children that must be opened.
-template <int KINDS, bool GRAD, bool COUNT>
-__device__ __forceinline__ void packet_record(const SdParams& P, float3 q, float3 nq3, bool mine, int rec, Lse& acc,
-                                              const WarpShared& ws, int& nq, int lane, int& ntest, int& nfar,
-                                              int& nleaf, int& ref0, int& ref1, unsigned& open0, unsigned& open1)
+template <int KINDS, bool GRAD, bool COUNT, int QK>
+__device__ __forceinline__ void packet_record(const SdParams& P, float3 q, float3 nq3, int qi, const QPrims& QP,
+                                              bool mine, int rec, Lse& acc, const WarpShared& ws, int& nq, int lane,
+                                              int& ntest, int& nfar, int& nleaf, int& ref0, int& ref1,
+                                              unsigned& open0, unsigned& open1)
 {
     const SdNode& r = P.nodes[rec];
     float4 a = __ldg(&r.a), b = __ldg(&r.b), c = __ldg(&r.c);
@@ -176,21 +208,23 @@ __device__ __forceinline__ void packet_record(const SdParams& P, float3 q, float
     ref1 = d.y;
     open0 = open1 = 0u;
     if (nm0) {
-        if (d.x < 0) queue_leaf<KINDS, GRAD>(P, q, near0, nm0, d.x, acc, ws, nq, lane, nleaf);
+        if (d.x < 0) queue_leaf<KINDS, GRAD, QK>(P, q, qi, QP, near0, nm0, d.x, acc, ws, nq, lane, nleaf);
         else open0 = nm0;
     }
     if (nm1) {
-        if (d.y < 0) queue_leaf<KINDS, GRAD>(P, q, near1, nm1, d.y, acc, ws, nq, lane, nleaf);
+        if (d.y < 0) queue_leaf<KINDS, GRAD, QK>(P, q, qi, QP, near1, nm1, d.y, acc, ws, nq, lane, nleaf);
         else open1 = nm1;
     }
 }
 
-template <int KINDS, bool GRAD, bool COUNT>
+// QK = 1: point queries q[3 qi..]; QK = 2, 3: query primitive qi of QP,
+// whose Barnes-Hut tests take its axis-aligned box [q, -nq3] (Sec. 3.5).
+template <int KINDS, bool GRAD, bool COUNT, int QK>
 __global__ void __launch_bounds__(PK_MAX_THREADS) k_traverse(SdParams P, const float* __restrict__ qs, int M,
                                                              const int* __restrict__ order,
                                                              float* __restrict__ value, float* __restrict__ grad,
                                                              int* __restrict__ counts, int* __restrict__ status,
-                                                             int* __restrict__ work, int npackets)
+                                                             int* __restrict__ work, int npackets, QPrims QP)
 {
     extern __shared__ int smem_i[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -209,16 +243,35 @@ __global__ void __launch_bounds__(PK_MAX_THREADS) k_traverse(SdParams P, const f
         const int t = pkt * 32 + lane;
         const bool inrange = t < M;
         int qi = inrange ? (order ? order[t] : t) : 0;
-        float3 q = f3(0.f, 0.f, 0.f);
-        if (inrange) q = f3(qs[3 * qi], qs[3 * qi + 1], qs[3 * qi + 2]);
-        bool ok = inrange && isfinite(q.x) && isfinite(q.y) && isfinite(q.z);
+        float3 q = f3(0.f, 0.f, 0.f), qhi = q;
+        bool ok = inrange;
+        bool bad_index = false;
+        if (inrange) {
+            if (QK == 1) {
+                q = qhi = f3(qs[3 * qi], qs[3 * qi + 1], qs[3 * qi + 2]);
+            } else {
+                q = f3(INFINITY, INFINITY, INFINITY);
+                qhi = f3(-INFINITY, -INFINITY, -INFINITY);
+                for (int c = 0; c < QK; ++c) {
+                    int vi = QP.F[QK * qi + c];
+                    if (vi < 0 || vi >= QP.nv) { bad_index = true; continue; }
+                    float3 g = f3(QP.V[3 * vi], QP.V[3 * vi + 1], QP.V[3 * vi + 2]);
+                    q = f3(fminf(q.x, g.x), fminf(q.y, g.y), fminf(q.z, g.z));
+                    qhi = f3(fmaxf(qhi.x, g.x), fmaxf(qhi.y, g.y), fmaxf(qhi.z, g.z));
+                    if (!(isfinite(g.x) && isfinite(g.y) && isfinite(g.z))) ok = false;
+                }
+                ok = ok && !bad_index;
+            }
+            ok = ok && isfinite(q.x) && isfinite(q.y) && isfinite(q.z) && isfinite(qhi.x) && isfinite(qhi.y) &&
+                 isfinite(qhi.z);
+        }
         if (inrange && !ok) {
-            atomicOr(status, 1 << SD_ERR_NONFINITE);
+            atomicOr(status, 1 << (bad_index ? SD_ERR_INDEX : SD_ERR_NONFINITE));
             value[qi] = __int_as_float(0x7fffffff);
             if (grad) grad[3 * qi] = grad[3 * qi + 1] = grad[3 * qi + 2] = __int_as_float(0x7fffffff);
             if (counts) counts[3 * qi] = counts[3 * qi + 1] = counts[3 * qi + 2] = 0;
         }
-        if (!ok) q = f3(0.f, 0.f, 0.f);
+        if (!ok) q = qhi = f3(0.f, 0.f, 0.f);
         unsigned mask = __ballot_sync(0xffffffffu, ok);
         if (!mask) continue;
         Lse acc;
@@ -227,13 +280,13 @@ __global__ void __launch_bounds__(PK_MAX_THREADS) k_traverse(SdParams P, const f
         bool overflow = false;
         int sp = 0, nq = 0;
         int rec = P.root_record;
-        const float3 nq3 = f3(-q.x, -q.y, -q.z);
+        const float3 nq3 = f3(-qhi.x, -qhi.y, -qhi.z);
         for (;;) {
             const bool mine = (mask >> lane) & 1u;
             int r0, r1;
             unsigned o0, o1;
-            packet_record<KINDS, GRAD, COUNT>(P, q, nq3, mine, rec, acc, ws, nq, lane, ntest, nfar, nleaf, r0, r1,
-                                              o0, o1);
+            packet_record<KINDS, GRAD, COUNT, QK>(P, q, nq3, qi, QP, mine, rec, acc, ws, nq, lane, ntest, nfar,
+                                                  nleaf, r0, r1, o0, o1);
             // descend into a child that must be opened; keep the other on the stack
             if (o0) {
                 if (o1) {
@@ -261,7 +314,7 @@ __global__ void __launch_bounds__(PK_MAX_THREADS) k_traverse(SdParams P, const f
             rec = e.x;
             mask = (unsigned)e.y;
         }
-        if (nq > 0) flush_queue<KINDS, GRAD>(P, q, ws.queue, nq, ws, lane, acc);
+        if (nq > 0) flush_queue<KINDS, GRAD, QK>(P, q, qi, QP, ws.queue, nq, ws, lane, acc);
         if (overflow && lane == 0) atomicOr(status, 1 << SD_ERR_TOO_LARGE);
         if (!ok) continue;
         // Alg. 2: d^ = -log(c)/alpha, grad d^ = grad c / c (c >= 1 after the shift)
@@ -406,6 +459,21 @@ int sm_count()
     return cached[dev];
 }
 
+// persistent traversal launch: one block per resident slot on every SM
+template <int KINDS, bool GRAD, bool COUNT, int QK>
+void launch_traverse(const sd_tree* t, const float* q, int M, const int* order, float* value, float* grad,
+                     int* counts, int block, int* work, const QPrims& QP, cudaStream_t st)
+{
+    int B = block > 0 ? block : 128;
+    size_t smem = sizeof(int) * PK_WARP_INTS * (B / 32);
+    int npackets = (M + 31) / 32;
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_traverse<KINDS, GRAD, COUNT, QK>, B, smem);
+    int blocks = std::max(1, std::min(per_sm * sm_count(), (npackets * 32 + B - 1) / B));
+    k_traverse<KINDS, GRAD, COUNT, QK><<<blocks, B, smem, st>>>(t->P, q, M, order, value, grad, counts, t->status,
+                                                                work, npackets, QP);
+}
+
 template <bool BRUTE, int KINDS, bool GRAD>
 void launch_one(const sd_tree* t, const float* q, int M, const int* order, float* value, float* grad, int* counts,
                 int block, int* work, cudaStream_t st)
@@ -413,22 +481,27 @@ void launch_one(const sd_tree* t, const float* q, int M, const int* order, float
     if (BRUTE) {
         k_brute<KINDS, GRAD><<<(M + BT - 1) / BT, BT, 0, st>>>(t->P, q, M, value, grad, t->status);
     } else {
-        int B = block > 0 ? block : 128;
-        size_t smem = sizeof(int) * PK_WARP_INTS * (B / 32);
-        int npackets = (M + 31) / 32;
-        int per_sm = 0;
-        if (counts) {
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_traverse<KINDS, GRAD, true>, B, smem);
-            int blocks = std::max(1, std::min(per_sm * sm_count(), (npackets * 32 + B - 1) / B));
-            k_traverse<KINDS, GRAD, true><<<blocks, B, smem, st>>>(t->P, q, M, order, value, grad, counts,
-                                                                   t->status, work, npackets);
-        } else {
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_traverse<KINDS, GRAD, false>, B, smem);
-            int blocks = std::max(1, std::min(per_sm * sm_count(), (npackets * 32 + B - 1) / B));
-            k_traverse<KINDS, GRAD, false><<<blocks, B, smem, st>>>(t->P, q, M, order, value, grad, counts,
-                                                                    t->status, work, npackets);
-        }
+        QPrims none{nullptr, nullptr, 0};
+        if (counts) launch_traverse<KINDS, GRAD, true, 1>(t, q, M, order, value, grad, counts, block, work, none, st);
+        else launch_traverse<KINDS, GRAD, false, 1>(t, q, M, order, value, grad, counts, block, work, none, st);
     }
+}
+
+// edge (QK = 2) or triangle (QK = 3) queries; value and gradient always
+template <int QK>
+void dispatch_prims(const sd_tree* t, const QPrims& QP, int M, const int* order, float* value, float* grad,
+                    int* counts, int block, int* work, cudaStream_t st)
+{
+#define SD_LAUNCH_PRIMS(K)                                                                                     \
+    (counts ? launch_traverse<K, true, true, QK>(t, nullptr, M, order, value, grad, counts, block, work, QP, st) \
+            : launch_traverse<K, true, false, QK>(t, nullptr, M, order, value, grad, counts, block, work, QP, st))
+    switch (t->kinds) {
+    case SD_HAS_PTS: SD_LAUNCH_PRIMS(SD_HAS_PTS); break;
+    case SD_HAS_SEGS: SD_LAUNCH_PRIMS(SD_HAS_SEGS); break;
+    case SD_HAS_TRIS: SD_LAUNCH_PRIMS(SD_HAS_TRIS); break;
+    default: SD_LAUNCH_PRIMS(7); break;
+    }
+#undef SD_LAUNCH_PRIMS
 }
 
 template <bool BRUTE>
@@ -547,6 +620,84 @@ extern "C" int sd_query(const sd_tree* t, const float* q, int64_t M, float* valu
     e = cudaGetLastError();
     cudaFreeAsync(tmp, st);
     return sd_cuda_status(e);
+}
+
+namespace {
+
+// centroid of each query primitive (the traversal order key, and the query
+// point itself when k = 1); a primitive with an index outside [0, nv) is
+// reported in the status word and gets the origin (k = 1: NaN, so that the
+// point traversal skips it)
+__global__ void k_prim_centroids(const float* __restrict__ V, const int* __restrict__ F, int k, int m, int nv,
+                                 float* __restrict__ c, int* status)
+{
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= m) return;
+    float s[3] = {0.f, 0.f, 0.f};
+    bool ok = true;
+    for (int i = 0; i < k; ++i) {
+        int v = F[k * j + i];
+        if (v < 0 || v >= nv) { ok = false; continue; }
+        for (int d = 0; d < 3; ++d) s[d] += V[3 * v + d];
+    }
+    const float inv = k == 1 ? 1.f : (k == 2 ? 0.5f : 1.f / 3.f);
+    if (!ok) atomicOr(status, 1 << SD_ERR_INDEX);
+    const float bad = k == 1 ? __int_as_float(0x7fffffff) : 0.f;
+    for (int d = 0; d < 3; ++d) c[3 * j + d] = ok ? s[d] * inv : bad;
+}
+
+}  // namespace
+
+extern "C" int sd_query_prims(const sd_tree* t, const float* QV, int64_t nqv, const int32_t* QF, int32_t k, int64_t M,
+                              float* value, float* grad, const sd_query_opts* opts_in, void* stream)
+{
+    if (!t || k < 1 || k > 3 || M < 0 || nqv < 0 || (M > 0 && (!QV || !QF || !value))) return SD_ERR_INVALID_ARG;
+    if (M >= ((int64_t)1 << 31) / 3 || nqv >= ((int64_t)1 << 31) / 3) return SD_ERR_TOO_LARGE;
+    SdUse use_{t, (cudaStream_t)stream};
+    sd_query_opts opts;
+    if (opts_in) opts = *opts_in; else sd_default_query_opts(&opts);
+    if (opts.block < 0 || opts.block > PK_MAX_THREADS || (opts.block % 32) != 0) return SD_ERR_INVALID_ARG;
+    if (M == 0) return SD_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int m = (int)M;
+    if (t->info.n_prims == 0) {
+        k_fill_empty<<<(m + 255) / 256, 256, 0, st>>>(value, grad, m);
+        sd_count_launches(1);
+        if (opts.counts) cudaMemsetAsync(opts.counts, 0, sizeof(int) * 3 * (size_t)m, st);
+        return sd_cuda_status(cudaGetLastError());
+    }
+    const int* order = opts.order;
+    const bool sort = !order && opts.sort_queries && m > 1;
+    // scratch: packet counter, centroids, order, gradient when not wanted
+    size_t o_cent = 256, o_ord = o_cent + 16 * (((size_t)m * 3 * sizeof(float) + 15) / 16);
+    size_t o_grad = o_ord + 16 * (((size_t)m * sizeof(int) + 15) / 16);
+    size_t bytes = o_grad + (grad ? 0 : sizeof(float) * 3 * (size_t)m);
+    void* tmp = nullptr;
+    cudaError_t e = cudaMallocAsync(&tmp, bytes, st);
+    if (e != cudaSuccess) { cudaGetLastError(); return SD_ERR_OOM; }
+    int* work = (int*)tmp;
+    float* cent = (float*)((char*)tmp + o_cent);
+    int32_t* ord = (int32_t*)((char*)tmp + o_ord);
+    float* g = grad ? grad : (float*)((char*)tmp + o_grad);
+    cudaMemsetAsync(work, 0, sizeof(int), st);
+    k_prim_centroids<<<(m + 255) / 256, 256, 0, st>>>(QV, QF, k, m, (int)nqv, cent, t->status);
+    int nl = 1;
+    int rc = SD_OK;
+    if (sort) {
+        rc = compute_order(t, cent, m, ord, st);
+        order = ord;
+    }
+    if (rc == SD_OK) {
+        QPrims QP{QV, QF, (int)nqv};
+        if (k == 1) dispatch<false>(t, cent, m, order, value, g, opts.counts, opts.block, work, st);
+        else if (k == 2) dispatch_prims<2>(t, QP, m, order, value, g, opts.counts, opts.block, work, st);
+        else dispatch_prims<3>(t, QP, m, order, value, g, opts.counts, opts.block, work, st);
+        ++nl;
+    }
+    sd_count_launches(nl);
+    e = cudaGetLastError();
+    cudaFreeAsync(tmp, st);
+    return rc != SD_OK ? rc : sd_cuda_status(e);
 }
 
 extern "C" int sd_query_brute(const sd_tree* t, const float* q, int64_t M, float* value, float* grad,
