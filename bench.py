@@ -342,7 +342,62 @@ def _extras(args, c, V, F, q, dev, M):
     res["pose"] = _pose_leg(args, dev)
     res["batch"] = _batch_leg(args, dev)
     res["surrogate"] = _surrogate_leg(args, dev)
+    res["query_mesh"] = _mesh_leg(args, dev)
     return res
+
+
+def _mesh_leg(args, dev, reps=10):
+    """Triangle queries (Sec. 3.4) and the query-mesh objective (Sec. 3.6) on
+    the street (2,000,000 points + 50,000 wire segments, alpha 50, beta 0.5):
+    the 200,000 triangles of the posed 100,002-vertex body as query
+    primitives; one evaluation = sd_query_prims (value + translation
+    gradient per triangle) + sd_mesh_reduce (D, alpha_q = 100, and the
+    per-vertex gradients). Also the triangles' work counts."""
+    import torch
+
+    from paper_2108_10480_gb300 import SmoothDistance, mesh_reduce
+    s = _street()
+    b = synth.config3_body()
+    R = _rotation(b["theta"])
+    Vq = (b["V0"].astype(np.float64) @ R.T + b["p"]).astype(np.float32)
+    sd = SmoothDistance(points=s["points"], edges=(s["wire_V"], s["wire_E"]), alpha=50.0, beta=0.5, device=dev)
+    Vt = torch.from_numpy(Vq).to(dev)
+    Ft = torch.from_numpy(b["F"].astype(np.int32)).to(dev)
+    m = Ft.shape[0]
+    val = torch.empty(m, device=dev)
+    grad = torch.empty(m, 3, device=dev)
+
+    def one():
+        sd.query_prims(Vt, Ft, out=(val, grad))
+        return mesh_reduce(Ft, Vt.shape[0], val, grad, 100.0)
+    for _ in range(3):
+        one()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        D, vg = one()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    _, _, cnt = sd.query_prims(Vt, Ft, counts=True)
+    per = cnt.to(torch.float64).mean(0).tolist()
+    return {"what": "street, the posed 100,002-vertex body's 200,000 triangles as queries: "
+                    "sd_query_prims + sd_mesh_reduce (alpha_q 100)",
+            "triangles": m, "ms_per_evaluation": ms, "value": m / (ms / 1e3), "unit": "triangle queries/s",
+            "D": float(D.item()), "work_per_triangle": {"bh_tests": per[0], "far_accepts": per[1], "leaf_prims": per[2]},
+            "status": sd.status()}
+
+
+def _rotation(theta):
+    """Rotation matrix of a rotation vector (Rodrigues)."""
+    th = np.asarray(theta, np.float64)
+    t = float(np.linalg.norm(th))
+    K = np.array([[0.0, -th[2], th[1]], [th[2], 0.0, -th[0]], [-th[1], th[0], 0.0]])
+    if t < 1e-12:
+        return np.eye(3) + K
+    return np.eye(3) + np.sin(t) / t * K + (1 - np.cos(t)) / (t * t) * K @ K
 
 
 def _surrogate_leg(args, dev, reps=3):
