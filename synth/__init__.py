@@ -27,7 +27,7 @@ __all__ = [
     "points_on_sphere", "uniform_box", "icosphere", "perturb_radial",
     "shell_queries", "geodesic_icosphere", "torus", "random_rotation",
     "street_scene", "config1", "config2", "config3_scene", "config3_body",
-    "config4_bodies", "surrogate_samples", "tiny_mesh",
+    "config4_bodies", "surrogate_samples", "tiny_mesh", "mesh_edges", "blob", "trace_camera",
 ]
 
 
@@ -446,3 +446,47 @@ def tiny_mesh(kind: str, seed: int = 0):
         E = np.stack([np.arange(24), np.arange(1, 25)], 1)
         return _f32(V), E.astype(np.int32)
     raise ValueError(kind)
+
+
+def mesh_edges(F):
+    """Unique undirected edges of a triangle mesh, [ne, 2] int32 (lower
+    index first, sorted)."""
+    F = np.asarray(F, np.int64)
+    E = np.concatenate([F[:, [0, 1]], F[:, [1, 2]], F[:, [2, 0]]])
+    E.sort(axis=1)
+    return np.unique(E, axis=0).astype(np.int32)
+
+
+def blob(level: int = 6, diag: float = 0.25, n_bumps: int = 12, seed: int = 6):
+    """A closed, bumpy, rabbit-sized stand-in for a scanned object: an
+    icosphere of the given level whose radius is modulated by a sum of
+    Gaussian bumps on the sphere (random centres, widths 0.25-0.6 rad,
+    heights -0.15..0.35), then scaled so that its bounding-box diagonal is
+    ``diag`` (0.25 m, the size of a desktop scan). Returns (V float32, F
+    int32)."""
+    rng = np.random.default_rng(seed)
+    V, F = icosphere(level)
+    u = V.astype(np.float64)
+    c = rng.normal(size=(n_bumps, 3))
+    c /= np.linalg.norm(c, axis=1, keepdims=True)
+    w = rng.uniform(0.25, 0.6, n_bumps)
+    h = rng.uniform(-0.15, 0.35, n_bumps)
+    ang = np.arccos(np.clip(u @ c.T, -1.0, 1.0))
+    r = 1.0 + (h * np.exp(-(ang / w) ** 2)).sum(1)
+    X = u * r[:, None] * np.array([1.0, 0.8, 0.9])
+    X *= diag / np.linalg.norm(X.max(0) - X.min(0))
+    return _f32(X), F
+
+
+def trace_camera(V, width: int = 512, height: int = 512, dist: float = 2.2, fov_deg: float = 30.0):
+    """A pinhole camera looking at the centre of V's bounding box from
+    ``dist`` bounding-box diagonals away (slightly above and to the side).
+    Returns dict(eye, target, up, fov_y, width, height, diag)."""
+    V = np.asarray(V, np.float64)
+    lo, hi = V.min(0), V.max(0)
+    c = 0.5 * (lo + hi)
+    diag = float(np.linalg.norm(hi - lo))
+    d = np.array([0.6, -1.0, 0.45])
+    d /= np.linalg.norm(d)
+    return dict(eye=c + dist * diag * d, target=c, up=np.array([0.0, 0.0, 1.0]), fov_y=math.radians(fov_deg),
+                width=int(width), height=int(height), diag=diag)
