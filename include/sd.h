@@ -299,6 +299,34 @@ int sd_query_prims(const sd_tree* t, const float* QV, int64_t nqv, const int32_t
 int sd_mesh_reduce(const int32_t* QF, int32_t k, int64_t M, int64_t nqv, const float* value, const float* grad,
                    float alpha_q, float* out, float* vgrad, int32_t* status, void* stream);
 
+/*
+ * Sphere tracing of the zero isosurface of d^ (Sec. 4.2; Hart 1996) through
+ * a pinhole camera. Pixel (row i from the top, column j) looks along
+ * normalize(f + x r + y u), f the unit view direction (target - eye), r the
+ * unit f x up, u = r x f, x = ((j + 0.5) / W * 2 - 1) tan(fov_y / 2) W / H,
+ * y = (1 - (i + 0.5) / H * 2) tan(fov_y / 2). Each ray starts at t = 0 from
+ * eye; at every step d^(eye + t dir) is evaluated (Barnes-Hut with the
+ * tree's alpha and beta, value only): d^ < eps is a hit at depth t,
+ * otherwise t += d^, and the ray misses once t > t_max or after max_steps
+ * evaluations.
+ *   depth  device [H*W] float32, row-major: hit depth, +inf for a miss
+ *   steps  device [H*W] int32 (may be NULL): evaluations spent on the ray
+ *   evaluations host int64 (may be NULL): evaluations over all rays
+ * Synchronises `stream` once per step (to size the next wavefront). Uses
+ * stream-ordered temporary memory.
+ */
+typedef struct {
+    float eye[3], target[3], up[3];
+    float fov_y;          /* vertical field of view, radians, (0, 3.1) */
+    int32_t width, height;
+    float eps;            /* > 0 */
+    float t_max;          /* > 0 */
+    int32_t max_steps;    /* > 0 */
+    int32_t block;        /* traversal block size, a multiple of 32 up to 256; 0 = default */
+} sd_trace_opts;
+int sd_sphere_trace(const sd_tree* t, const sd_trace_opts* opts, float* depth, int32_t* steps, int64_t* evaluations,
+                    void* stream);
+
 /* Synchronise `stream`, return and clear the tree's device status word. */
 int sd_query_status(const sd_tree* t, void* stream);
 

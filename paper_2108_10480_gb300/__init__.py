@@ -193,6 +193,25 @@ class SmoothDistance:
         _native.check(rc, "sd_query_prims")
         return (val, grad, cnt) if counts else (val, grad)
 
+    def sphere_trace(self, cam, eps=1e-5, t_max=1.0, max_steps=256, block=0, stream=None):
+        """Sphere-traced depth image of the zero isosurface (sd_sphere_trace).
+        cam: dict(eye, target, up, fov_y, width, height). Returns depth [H, W]
+        (+inf for misses), evaluations per ray [H, W] and their total."""
+        o = _native.SdTraceOpts()
+        for name in ("eye", "target", "up"):
+            getattr(o, name)[:] = [float(x) for x in cam[name]]
+        o.fov_y = float(cam["fov_y"])
+        o.width, o.height = int(cam["width"]), int(cam["height"])
+        o.eps, o.t_max, o.max_steps, o.block = float(eps), float(t_max), int(max_steps), int(block)
+        H, W = o.height, o.width
+        depth = torch.empty(H, W, device=self.device)
+        steps = torch.empty(H, W, dtype=torch.int32, device=self.device)
+        ev = ctypes.c_int64(0)
+        rc = lib().sd_sphere_trace(self._h, ctypes.byref(o), _ptr(depth), _ptr(steps), ctypes.byref(ev),
+                                   _stream_handle(stream))
+        _native.check(rc, "sd_sphere_trace")
+        return depth, steps, int(ev.value)
+
     def status(self, stream=None) -> int:
         """Synchronise and return (then clear) the device status word."""
         return lib().sd_query_status(self._h, _stream_handle(stream))

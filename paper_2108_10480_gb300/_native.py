@@ -43,6 +43,12 @@ class SdQueryOpts(ctypes.Structure):
     _fields_ = [("sort_queries", c_int32), ("block", c_int32), ("counts", c_void_p), ("order", c_void_p)]
 
 
+class SdTraceOpts(ctypes.Structure):
+    _fields_ = [("eye", c_float * 3), ("target", c_float * 3), ("up", c_float * 3), ("fov_y", c_float),
+                ("width", c_int32), ("height", c_int32), ("eps", c_float), ("t_max", c_float),
+                ("max_steps", c_int32), ("block", c_int32)]
+
+
 class SdTreeInfo(ctypes.Structure):
     _fields_ = [("n_prims", c_int64), ("n_points", c_int64), ("n_edges", c_int64), ("n_tris", c_int64),
                 ("n_buckets", c_int64), ("leaf_size", c_int32),
@@ -89,6 +95,8 @@ SIGNATURES = {
                                       c_void_p, ctypes.POINTER(SdQueryOpts), c_void_p]),
     "sd_mesh_reduce": (ctypes.c_int, [c_void_p, ctypes.c_int32, c_int64, c_int64, c_void_p, c_void_p, c_float,
                                       c_void_p, c_void_p, c_void_p, c_void_p]),
+    "sd_sphere_trace": (ctypes.c_int, [c_void_p, ctypes.POINTER(SdTraceOpts), c_void_p, c_void_p,
+                                       ctypes.POINTER(c_int64), c_void_p]),
     "sd_lower_bound": (ctypes.c_int, [c_void_p, c_void_p, c_int64, c_float, c_void_p, c_void_p, c_void_p, c_void_p]),
     "sd_surrogate_query": (ctypes.c_int, [c_void_p, c_void_p, c_void_p, c_float, c_void_p, c_int64, c_void_p,
                                           c_void_p, c_void_p, ctypes.POINTER(c_int64), c_void_p]),
