@@ -343,7 +343,64 @@ def _extras(args, c, V, F, q, dev, M):
     res["batch"] = _batch_leg(args, dev)
     res["surrogate"] = _surrogate_leg(args, dev)
     res["query_mesh"] = _mesh_leg(args, dev)
+    res["sphere_trace"] = _trace_leg(args, dev)
     return res
+
+
+def _trace_leg(args, dev, betas=(0.1, 0.2, 0.3, 0.5, 0.75, 1.0)):
+    """The paper's beta study (Sec. 4.3, parameter analysis) on a synthetic
+    stand-in for a desktop scan: a bumpy closed mesh of 20,480 triangles
+    (10,242 vertices, 30,720 edges, bounding-box diagonal 0.25 m) taken as its
+    vertices, its edges or its triangles; alpha 200, alpha_U 1200. Time to
+    sphere-trace a 512 x 512 image at each beta, and the isosurface error:
+    |depth(beta) - depth(0)| / diagonal over the rays that hit at both,
+    measured on a 128 x 128 image of the same camera (the exact render at
+    beta = 0 is 16x cheaper there; its 512 x 512 time is that render's time
+    x 16, marked as scaled)."""
+    import torch
+
+    from paper_2108_10480_gb300 import SmoothDistance
+    V, F = synth.blob(level=5)
+    E = synth.mesh_edges(F)
+    cam = synth.trace_camera(V, 512, 512)
+    small = dict(cam, width=128, height=128)
+    t_max = 4.0 * cam["diag"]
+    out = {"what": "512x512 sphere-traced renders of a 20,480-triangle bumpy mesh (diag 0.25 m) as vertices, "
+                   "edges or triangles, alpha 200, alpha_U 1200, eps 1e-5 m; error on 128x128 vs beta 0",
+           "kinds": {}}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stream = torch.cuda.current_stream()
+    for kind, kw in (("vertices", dict(points=V)), ("edges", dict(edges=(V, E))), ("triangles", dict(tris=(V, F)))):
+        ref = SmoothDistance(alpha=200.0, alpha_u=1200.0, beta=0.0, device=dev, **kw)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        d0, _, ev0 = ref.sphere_trace(small, eps=1e-5, t_max=t_max)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms0 = e0.elapsed_time(e1)
+        d0 = d0.cpu().numpy()
+        rows = [{"beta": 0.0, "ms_512": 16 * ms0, "ms_512_scaled_from_128": True, "evaluations_128": ev0,
+                 "evals_per_s": ev0 / (ms0 / 1e3), "err_mean_rel_diag": 0.0, "err_max_rel_diag": 0.0,
+                 "hit_mismatch_frac": 0.0}]
+        for beta in betas:
+            sd = SmoothDistance(alpha=200.0, alpha_u=1200.0, beta=beta, device=dev, **kw)
+            sd.sphere_trace(cam, eps=1e-5, t_max=t_max)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            _, steps, ev = sd.sphere_trace(cam, eps=1e-5, t_max=t_max)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            db, _, _ = sd.sphere_trace(small, eps=1e-5, t_max=t_max)
+            db = db.cpu().numpy()
+            both = np.isfinite(d0) & np.isfinite(db)
+            err = np.abs(db[both] - d0[both]) / cam["diag"]
+            rows.append({"beta": beta, "ms_512": ms, "evaluations_512": ev,
+                         "evals_per_s": ev / (ms / 1e3),
+                         "err_mean_rel_diag": float(err.mean()), "err_max_rel_diag": float(err.max()),
+                         "hit_mismatch_frac": float((np.isfinite(d0) != np.isfinite(db)).mean())})
+        out["kinds"][kind] = rows
+    return out
 
 
 def _mesh_leg(args, dev, reps=10):
