@@ -344,7 +344,133 @@ def _extras(args, c, V, F, q, dev, M):
     res["surrogate"] = _surrogate_leg(args, dev)
     res["query_mesh"] = _mesh_leg(args, dev)
     res["sphere_trace"] = _trace_leg(args, dev)
+    res["voxel_grid"] = _voxel_leg(args, dev)
+    res["beta_switch"] = _switch_leg(args, dev)
     return res
+
+
+def _unit_box(X):
+    """Scale and translate so the bounding box is centred at (0.5, 0.5, 0.5)
+    with diagonal 0.5 (the voxel benchmark's normalisation)."""
+    X = np.asarray(X, np.float64)
+    lo, hi = X.min(0), X.max(0)
+    return ((X - 0.5 * (lo + hi)) * (0.5 / np.linalg.norm(hi - lo)) + 0.5).astype(np.float32)
+
+
+def _voxel_leg(args, dev):
+    """The performance benchmark of Sec. 4.4 on synthetic meshes (bumpy
+    spheres and tori, 80 to 81,920 triangles) in place of Thingi10K: each
+    mesh as its vertices V, edges E and triangles F, scaled into a box of
+    diagonal 0.5 centred in the unit cube; d^ and its gradient at the
+    1,000,000 voxel centres of a 100^3 grid over [0, 1]^3, beta 0.5, alpha
+    by the paper's heuristic (1 / shortest edge for E and F, 100 x the
+    bounding-box diagonal for V). Leaves visited = exact primitive terms +
+    far-field expansions per query."""
+    import torch
+
+    from paper_2108_10480_gb300 import SmoothDistance
+    g = (np.arange(100) + 0.5) / 100
+    q = torch.from_numpy(np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3).astype(np.float32)).to(dev)
+    M = q.shape[0]
+    meshes = [("blob", lvl) + synth.blob(level=lvl, diag=1.0, seed=10 + lvl) for lvl in (1, 2, 3, 4, 5, 6)]
+    meshes += [("torus", n) + synth.torus(n, max(6, n // 3), 1.0, 0.3) for n in (12, 40, 120, 360)]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stream = torch.cuda.current_stream()
+    rows = []
+    for name, size, V, F in meshes:
+        V = _unit_box(V)
+        E = synth.mesh_edges(F)
+        emin = float(np.linalg.norm(V[E[:, 0]] - V[E[:, 1]], axis=1).min())
+        for kind, kw, alpha in (("V", dict(points=V), 100 * 0.5), ("E", dict(edges=(V, E)), 1.0 / emin),
+                                ("F", dict(tris=(V, F)), 1.0 / emin)):
+            sd = SmoothDistance(alpha=alpha, beta=0.5, device=dev, **kw)
+            sd.query(q)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            sd.query(q)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            _, _, cnt = sd.query(q, counts=True)
+            leaves = (cnt[:, 1] + cnt[:, 2]).to(torch.float64)
+            n = int(sd.info()["n_prims"])
+            rows.append({"mesh": f"{name}-{size}", "kind": kind, "n_prims": n, "alpha": alpha, "ms": ms,
+                         "queries_per_s": M / (ms / 1e3), "leaves_visited_mean": float(leaves.mean()),
+                         "leaves_visited_max": int(leaves.max()),
+                         "leaves_visited_pct_mean": float(100.0 * leaves.mean() / n)})
+    return {"what": "100^3 voxel centres, d^ + gradient, beta 0.5, synthetic meshes as V / E / F "
+                    "(box diagonal 0.5 in the unit cube)", "rows": rows}
+
+
+def _switch_leg(args, dev, iso=0.1, probes=4096, dz=2e-3, steps=400):
+    """The beta sensitivity study of Sec. 4.3 on the street (2,000,000 points,
+    alpha 50): vertical rays from uniform points on the top and bottom of the
+    scene box are sphere-traced (in z) down or up to the d^ = 0.1 isosurface;
+    from there short vertical marches of 2 mm steps look for points where the
+    Barnes-Hut work of beta = 0.5 changes (the evaluation enters a node it
+    took as a far field before); at each such point where beta = 0.5001
+    traverses less of the tree, the values and gradients of the two betas are
+    compared."""
+    import torch
+
+    from paper_2108_10480_gb300 import SmoothDistance
+    s = _street()
+    P = s["points"]
+    sd0 = SmoothDistance(points=P, alpha=50.0, beta=0.5, device=dev)
+    sd1 = SmoothDistance(points=P, alpha=50.0, beta=0.5001, device=dev)
+    lo, hi = P.min(0), P.max(0)
+    rng = np.random.default_rng(31)
+    xy = lo[:2] + (hi[:2] - lo[:2]) * rng.random((probes, 2))
+    top = rng.random(probes) < 0.5
+    z = np.where(top, hi[2] + 1.0, lo[2] - 1.0)
+    sgn = np.where(top, -1.0, 1.0)
+    pts = torch.from_numpy(np.stack([xy[:, 0], xy[:, 1], z], 1).astype(np.float32)).to(dev)
+    dirz = torch.from_numpy(sgn.astype(np.float32)).to(dev)
+    alive = torch.ones(probes, dtype=torch.bool, device=dev)
+    done = torch.zeros(probes, dtype=torch.bool, device=dev)
+    zlim = float(hi[2] - lo[2]) + 3.0
+    travel = torch.zeros(probes, device=dev)
+    for _ in range(200):
+        idx = torch.nonzero(alive & ~done).squeeze(1)
+        if idx.numel() == 0:
+            break
+        v, _ = sd0.query(pts[idx], grad=False)
+        hit = v <= iso
+        done[idx[hit]] = True
+        step = v.clamp_min(0) - iso + 1e-4
+        move = idx[~hit]
+        pts[move, 2] += dirz[move] * step[~hit]
+        travel[move] += step[~hit]
+        alive[move[travel[move] > zlim]] = False
+    start = pts[done]
+    dz_t = dirz[done]
+    found = []
+    prev = None
+    for k in range(steps):
+        x = start.clone()
+        x[:, 2] += dz_t * dz * k
+        _, _, c0 = sd0.query(x, counts=True)
+        if prev is not None:
+            sw = torch.nonzero((c0 != prev).any(1)).squeeze(1)
+            if sw.numel():
+                found.append(x[sw])
+        prev = c0
+    if not found:
+        return {"what": "beta 0.5 vs 0.5001 at far/near switch points", "points": 0}
+    X = torch.cat(found)
+    v0, g0, c0 = sd0.query(X, counts=True)
+    v1, g1, c1 = sd1.query(X, counts=True)
+    less = c1[:, 0] < c0[:, 0]
+    dv = (v1 - v0).abs()[less].double()
+    cos = torch.nn.functional.cosine_similarity(g0[less], g1[less], dim=1).double()
+    return {"what": "street points, alpha 50: d^ = 0.1 isosurface reached by vertical sphere tracing, then "
+                    "2 mm vertical marches; points where beta 0.5's traversal changes and beta 0.5001 tests fewer "
+                    "nodes", "rays_reaching_isosurface": int(done.sum()), "switch_points": int(X.shape[0]),
+            "points_compared": int(less.sum()),
+            "value_discrepancy": {"mean": float(dv.mean()) if dv.numel() else None,
+                                  "max": float(dv.max()) if dv.numel() else None},
+            "gradient_cosine": {"mean": float(cos.mean()) if cos.numel() else None,
+                                "min": float(cos.min()) if cos.numel() else None}}
 
 
 def _trace_leg(args, dev, betas=(0.1, 0.2, 0.3, 0.5, 0.75, 1.0)):
