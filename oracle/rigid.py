@@ -13,13 +13,16 @@ Readings of the paper's description:
   * The identity Hessian is taken in mass-normalised coordinates y = M^(1/2) x,
     where it is E's exact Hessian; only the constraint's curvature is left out.
   * One constraint c(x) = D(x) >= 0 (the query mesh's smooth distance, Eq.
-    lse_full2), a slack s >= 0 with multiplier lambda; barrier mu, shrunk by
-    10 once the KKT residual at mu falls below mu; steps cut to 0.995 of the
-    way to the s, lambda boundary, then halved until c(x) > 0 and the l1
-    merit function f - mu log s + nu |c - s| (nu = 2 lambda + 1) decreases by
-    the Armijo fraction 1e-4 of its directional derivative (the standard
-    globalisation of a primal-dual step; with W = I the step is a descent
-    direction of that merit function).
+    lse_full2), a slack s with multiplier lambda; the slack is reset to c at
+    every iterate (the constraint is evaluated exactly, so s = c is feasible
+    and the linearisation error of a curved c never enters the merit);
+    barrier mu, shrunk by 10 once the KKT residual at mu falls below mu; the
+    multiplier step cut to 0.995 of the way to its boundary; the primal step
+    (also cut so the linearised c stays above 0.005 c) halved until c(x) > 0
+    and the barrier function f - mu log c decreases by the Armijo fraction
+    1e-4 of its directional derivative. With s = c and W = I the primal-dual
+    step is dy = -(I + (lambda / c) a a^T)^-1 grad(f - mu log c), a descent
+    direction of that barrier function.
   * Every iterate has c(x) > 0. The distance is unsigned and there is no
     continuous collision detection (as in the paper), so a step that jumps
     through the data mesh by more than the smooth offset (about log n / alpha
@@ -62,47 +65,42 @@ def ipm_step(constraint, x_t, x_pred, Mdiag, r_max, mu0=1e-4, mu_min=1e-9, tol=1
     evals = 1
     if not c > 0:
         raise ValueError("the step must start from a feasible pose")
-    s, lam, mu = c, mu0 / c, mu0
+    lam, mu = mu0 / c, mu0
     it = 0
     for it in range(1, max_iter + 1):
         a = dc / sq
         g = y - y_pred
-        kkt = max(np.linalg.norm(g - lam * a), abs(lam * s - mu), abs(c - s))
+        kkt = max(np.linalg.norm(g - lam * a), abs(lam * c - mu))
         if kkt < max(mu, tol):
             if mu <= mu_min and kkt < tol:
                 break
             mu = max(mu / 10.0, mu_min)
-        dy, ds, dl = newton_direction(g, a, lam, s, c, mu)
-        # fraction to the boundary for s and lambda
-        al_s = 1.0 if ds >= 0 else min(1.0, -0.995 * s / ds)
+        dy, ds, dl = newton_direction(g, a, lam, c, c, mu)
+        al = 1.0 if ds >= 0 else min(1.0, -0.995 * c / ds)
         al_l = 1.0 if dl >= 0 else min(1.0, -0.995 * lam / dl)
         if conservative:
             # no vertex may move farther than 0.9 c in the step
             dx = dy / sq
             reach = np.linalg.norm(dx[3:]) + r_max * np.linalg.norm(dx[:3])
             if reach > 0:
-                al_s = min(al_s, 0.9 * c / reach)
-        # merit line search (feasible iterates only)
-        nu = 2.0 * lam + 1.0
-        phi0 = 0.5 * (g @ g) - mu * np.log(s) + nu * abs(c - s)
-        dphi = g @ dy - mu / s * ds - nu * abs(c - s)
+                al = min(al, 0.9 * c / reach)
+        # Armijo on the barrier function over feasible iterates
+        B0 = 0.5 * (g @ g) - mu * np.log(c)
+        dB = g @ dy - mu / c * (a @ dy)
         accepted = False
-        while al_s >= 1e-12:
-            y_new = y + al_s * dy
-            s_new = s + al_s * ds
+        while al >= 1e-12:
+            y_new = y + al * dy
             c_new, dc_new = constraint(y_new / sq)
             evals += 1
-            if c_new > 0 and s_new > 0:
+            if c_new > 0:
                 gn = y_new - y_pred
-                phi = 0.5 * (gn @ gn) - mu * np.log(s_new) + nu * abs(c_new - s_new)
-                if phi <= phi0 + 1e-4 * al_s * min(dphi, 0.0):
+                if 0.5 * (gn @ gn) - mu * np.log(c_new) <= B0 + 1e-4 * al * min(dB, 0.0):
                     accepted = True
                     break
-            al_s *= 0.5
+            al *= 0.5
         if not accepted:
             break
         y, c, dc = y_new, c_new, dc_new
-        s = s_new
         lam = max(lam + al_l * dl, 1e-16)
     return y / sq, lam, it, evals
 
