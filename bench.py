@@ -346,7 +346,46 @@ def _extras(args, c, V, F, q, dev, M):
     res["sphere_trace"] = _trace_leg(args, dev)
     res["voxel_grid"] = _voxel_leg(args, dev)
     res["beta_switch"] = _switch_leg(args, dev)
+    res["rigid"] = _rigid_leg(args, dev)
     return res
+
+
+def _rigid_leg(args, dev, steps=8, h=0.005):
+    """Rigid-body time steps (Sec. 4.5, Eq. opt) of the 100,002-vertex body
+    against the street (2,000,000 points + 50,000 wires, alpha 50, beta 0.5,
+    alpha_q 100): the body starts where D = 2 cm, moving at (0.5, 0, -3) m/s
+    under gravity; each step is the interior-point solve, every constraint
+    evaluation one placement + query + reduction on the GPU."""
+    import torch
+
+    from paper_2108_10480_gb300 import SmoothDistance
+    from paper_2108_10480_gb300.rigid import RigidBody
+    s = _street()
+    b = synth.config3_body()
+    sd = SmoothDistance(points=s["points"], edges=(s["wire_V"], s["wire_E"]), alpha=50.0, beta=0.5, device=dev)
+    X0 = torch.from_numpy(b["V0"]).to(dev)
+    ax = np.array([2.0, 1.0, 0.7])
+    I_body = np.diag([(ax[1] ** 2 + ax[2] ** 2), (ax[0] ** 2 + ax[2] ** 2), (ax[0] ** 2 + ax[1] ** 2)]) / 5.0
+    body = RigidBody(sd, X0, 1.0, I_body, b["theta"], b["p"], v=(0.5, 0.0, -3.0))
+    lo, hi = float(b["p"][2]) - 3.0, float(b["p"][2]) + 3.0
+    for _ in range(40):
+        mid = 0.5 * (lo + hi)
+        D = body.constraint(np.concatenate([body.theta, [body.p[0], body.p[1], mid]]), 100.0)[0]
+        lo, hi = (lo, mid) if D > 0.02 else (mid, hi)
+    body.p[2] = hi
+    rows = []
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        ts = time.perf_counter()
+        info = body.step(h, (0.0, 0.0, -9.81), 100.0, max_iter=200)
+        torch.cuda.synchronize()
+        rows.append(dict(info, ms=1e3 * (time.perf_counter() - ts), D=float(info["D"]), lam=float(info["lambda"])))
+    total = time.perf_counter() - t0
+    ev = sum(r["evaluations"] for r in rows)
+    return {"what": "rigid time steps (h 5 ms) of the 100,002-vertex body falling onto the street; IPM with "
+                    "identity Hessian, constraint on the GPU", "steps": rows, "ms_per_step": 1e3 * total / steps,
+            "evaluations_per_step": ev / steps, "ms_per_evaluation": 1e3 * total / ev,
+            "min_D": min(r["D"] for r in rows)}
 
 
 def _unit_box(X):
@@ -478,51 +517,40 @@ def _trace_leg(args, dev, betas=(0.1, 0.2, 0.3, 0.5, 0.75, 1.0)):
     stand-in for a desktop scan: a bumpy closed mesh of 20,480 triangles
     (10,242 vertices, 30,720 edges, bounding-box diagonal 0.25 m) taken as its
     vertices, its edges or its triangles; alpha 200, alpha_U 1200. Time to
-    sphere-trace a 512 x 512 image at each beta, and the isosurface error:
-    |depth(beta) - depth(0)| / diagonal over the rays that hit at both,
-    measured on a 128 x 128 image of the same camera (the exact render at
-    beta = 0 is 16x cheaper there; its 512 x 512 time is that render's time
-    x 16, marked as scaled)."""
+    sphere-trace a 512 x 512 image at each beta (beta = 0, the exact render,
+    timed once without a warm-up run), and the isosurface error
+    |depth(beta) - depth(0)| / diagonal over the rays that hit at both."""
     import torch
 
     from paper_2108_10480_gb300 import SmoothDistance
     V, F = synth.blob(level=5)
     E = synth.mesh_edges(F)
     cam = synth.trace_camera(V, 512, 512)
-    small = dict(cam, width=128, height=128)
     t_max = 4.0 * cam["diag"]
     out = {"what": "512x512 sphere-traced renders of a 20,480-triangle bumpy mesh (diag 0.25 m) as vertices, "
-                   "edges or triangles, alpha 200, alpha_U 1200, eps 1e-5 m; error on 128x128 vs beta 0",
+                   "edges or triangles, alpha 200, alpha_U 1200, eps 1e-5 m; error vs the beta = 0 render",
            "kinds": {}}
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     stream = torch.cuda.current_stream()
-    for kind, kw in (("vertices", dict(points=V)), ("edges", dict(edges=(V, E))), ("triangles", dict(tris=(V, F)))):
-        ref = SmoothDistance(alpha=200.0, alpha_u=1200.0, beta=0.0, device=dev, **kw)
+
+    def timed(sd, warm):
+        if warm:
+            sd.sphere_trace(cam, eps=1e-5, t_max=t_max)
         torch.cuda.synchronize()
         e0.record(stream)
-        d0, _, ev0 = ref.sphere_trace(small, eps=1e-5, t_max=t_max)
+        d, _, ev = sd.sphere_trace(cam, eps=1e-5, t_max=t_max)
         e1.record(stream)
         torch.cuda.synchronize()
-        ms0 = e0.elapsed_time(e1)
-        d0 = d0.cpu().numpy()
-        rows = [{"beta": 0.0, "ms_512": 16 * ms0, "ms_512_scaled_from_128": True, "evaluations_128": ev0,
-                 "evals_per_s": ev0 / (ms0 / 1e3), "err_mean_rel_diag": 0.0, "err_max_rel_diag": 0.0,
-                 "hit_mismatch_frac": 0.0}]
+        return d.cpu().numpy(), ev, e0.elapsed_time(e1)
+    for kind, kw in (("vertices", dict(points=V)), ("edges", dict(edges=(V, E))), ("triangles", dict(tris=(V, F)))):
+        d0, ev0, ms0 = timed(SmoothDistance(alpha=200.0, alpha_u=1200.0, beta=0.0, device=dev, **kw), False)
+        rows = [{"beta": 0.0, "ms_512": ms0, "evaluations": ev0, "evals_per_s": ev0 / (ms0 / 1e3),
+                 "err_mean_rel_diag": 0.0, "err_max_rel_diag": 0.0, "hit_mismatch_frac": 0.0}]
         for beta in betas:
-            sd = SmoothDistance(alpha=200.0, alpha_u=1200.0, beta=beta, device=dev, **kw)
-            sd.sphere_trace(cam, eps=1e-5, t_max=t_max)
-            torch.cuda.synchronize()
-            e0.record(stream)
-            _, steps, ev = sd.sphere_trace(cam, eps=1e-5, t_max=t_max)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            ms = e0.elapsed_time(e1)
-            db, _, _ = sd.sphere_trace(small, eps=1e-5, t_max=t_max)
-            db = db.cpu().numpy()
+            db, ev, ms = timed(SmoothDistance(alpha=200.0, alpha_u=1200.0, beta=beta, device=dev, **kw), True)
             both = np.isfinite(d0) & np.isfinite(db)
             err = np.abs(db[both] - d0[both]) / cam["diag"]
-            rows.append({"beta": beta, "ms_512": ms, "evaluations_512": ev,
-                         "evals_per_s": ev / (ms / 1e3),
+            rows.append({"beta": beta, "ms_512": ms, "evaluations": ev, "evals_per_s": ev / (ms / 1e3),
                          "err_mean_rel_diag": float(err.mean()), "err_max_rel_diag": float(err.max()),
                          "hit_mismatch_frac": float((np.isfinite(d0) != np.isfinite(db)).mean())})
         out["kinds"][kind] = rows
