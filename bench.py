@@ -121,48 +121,78 @@ def _traffic(kernel_hash):
 
 
 class _Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons every 50 ms.
+    Started before the warm-up (nvidia-smi takes a moment to begin); only
+    the samples stamped inside the timed window [mark(), stop()] are kept,
+    widened to the nearest sample on each side when the window is shorter
+    than the sampling interval."""
+
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
     def __init__(self, index):
         self.p = None
+        self.t0 = None
         self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
         try:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
             self.p = subprocess.Popen(
-                ["nvidia-smi", "-i", str(index), "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,"
-                 "clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
-                 "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
-                 "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-lms", "200"],
-                stdout=self.f, stderr=subprocess.DEVNULL)
+                ["nvidia-smi", "-i", str(index), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "50"], stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.p = None
+            return
+        t_end = time.time() + 5.0
+        while time.time() < t_end and os.path.getsize(self.path) == 0 and self.p.poll() is None:
+            time.sleep(0.02)
+
+    def mark(self):
+        self.t0 = time.time()
+
+    @staticmethod
+    def _stamp(txt):
+        """nvidia-smi's local-time stamp "YYYY/MM/DD hh:mm:ss.fff" in epoch seconds."""
+        main, _, frac = txt.partition(".")
+        try:
+            return time.mktime(time.strptime(main, "%Y/%m/%d %H:%M:%S")) + (float("0." + frac) if frac else 0.0)
+        except ValueError:
+            return None
 
     def stop(self):
         if self.p is None:
             return None
+        t1 = time.time()
+        time.sleep(0.1)      # the sample that closes the window
         self.p.terminate()
         try:
             self.p.wait(timeout=5)
         except Exception:
             self.p.kill()
         self.f.close()
-        sm, mx, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        rows = []
         for line in open(self.path):
             parts = [x.strip() for x in line.split(",")]
-            if len(parts) < 9:
+            if len(parts) < 10:
                 continue
+            ts = self._stamp(parts[0])
             try:
-                sm.append(float(parts[1]))
-                mx.append(float(parts[2]))
+                rows.append((ts, float(parts[2]), float(parts[3]), [v.lower() == "active" for v in parts[6:10]]))
             except ValueError:
                 continue
-            for nm, v in zip(names, parts[5:9]):
-                if v.lower() == "active":
-                    reasons.add(nm)
-        if not sm:
+        if not rows:
             return None
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
-                "reasons": sorted(reasons)}
+        t0 = self.t0 if self.t0 is not None else t1
+        inside = [r for r in rows if r[0] is not None and t0 <= r[0] <= t1]
+        if not inside:
+            before = [r for r in rows if r[0] is not None and r[0] < t0]
+            after = [r for r in rows if r[0] is not None and r[0] > t1]
+            inside = before[-1:] + after[:1] or rows[-1:]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({nm for r in inside for nm, on in zip(names, r[3]) if on})
+        return {"sm_mhz": statistics.median(r[1] for r in inside), "sm_max_mhz": max(r[2] for r in inside),
+                "samples": len(inside), "interval_ms": 50, "reasons": reasons}
 
 
 def _max_over_ranks(ms, device):
@@ -226,6 +256,7 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
 
+    clocks = _Clocks(local) if rank == 0 else None
     for _ in range(max(args.warmup, 0)):
         step()
     # work counts of this workload (decisions are deterministic)
@@ -233,8 +264,9 @@ def run_ours(args):
     _, _, cnt = sd.query(q, counts=True)
     tot = cnt.to(torch.int64).sum(0).tolist()
     del sd
-    clocks = _Clocks(local) if rank == 0 else None
     barrier()
+    if clocks:
+        clocks.mark()
     launches0 = kernel_launches()
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
     t_wall = time.perf_counter()
