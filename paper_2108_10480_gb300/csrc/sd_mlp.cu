@@ -12,10 +12,10 @@
 // Training (sd_mlp_train_step): layer-by-layer fp32 SIMT GEMMs over a batch
 // in device memory, mean-squared-error gradient, Adam; every reduction runs
 // in a fixed order, so a step is deterministic.
-// Inference (sd_mlp_forward): one fused kernel per 16-query tile and warp,
-// bf16 tensor-core MMAs (mma.sync m16n8k16, fp32 accumulate), activations
-// kept in registers between layers, weights in shared memory, and the input
-// gradient dy/dx by back-propagation through the same weights.
+// Inference (sd_mlp_forward): one fused kernel per 128-query tile on the
+// tcgen05 tensor cores (bf16 operands in shared memory, fp32 accumulators in
+// tensor memory), weights staged once per CTA, and the input gradient dy/dx
+// by back-propagation through the same weights.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -207,296 +207,458 @@ __global__ void k_adam(float* __restrict__ P, const float* __restrict__ G, float
 }
 
 // ---------------------------------------------------------------------------
-// fused inference: bf16 tensor-core MLP, value and input gradient
+// fused inference on the 5th-generation tensor cores (tcgen05): value and
+// input gradient of 128-query tiles
 // ---------------------------------------------------------------------------
-constexpr int IW = 8;                   // warps per block
-constexpr int S1 = 88;                  // W1 row stride (bf16): 80 used columns, conflict-free ldmatrix
-constexpr int S2 = 136;                 // W2, W3 row stride (bf16)
-constexpr int FS = 81;                  // per-warp feature row stride (fp32): 80 columns
-constexpr int SMEM_W = HID * S1 + 2 * HID * S2;            // bf16 elements
-constexpr int SMEM_STASH = 2 * 16 * HID;                   // fp16 dsilu of layers 1, 2 per warp
-constexpr size_t SMEM_BYTES = sizeof(__nv_bfloat16) * SMEM_W + sizeof(float) * (4 * HID + 96 + 8) +
-                              (size_t)IW * (sizeof(float) * 16 * FS + sizeof(__half) * SMEM_STASH);
+// One CTA per SM; its 16 warps form two groups of 8 that walk alternate
+// 128-row tiles, so one group's activation work overlaps the other's tensor
+// work. The six GEMMs of a tile (three layers forward, three back for dy/dx)
+// are single-thread-issued tcgen05.mma (kind::f16, bf16 operands, fp32
+// accumulation, M = 128) with both operands in shared memory and the
+// accumulator in tensor memory (TMEM); completion is signalled through the
+// group's mbarrier by tcgen05.commit. Between GEMMs the group's 256 threads
+// (thread = TMEM lane (row) x half of the columns) read the accumulator with
+// tcgen05.ld, apply bias and activation and write the next A operand back to
+// the group's shared-memory buffer; dsilu(z1), dsilu(z2) wait in TMEM as
+// packed binary16 pairs (tcgen05.st) for the backward pass. Operands use the
+// no-swizzle layout of 8 x 16-byte core matrices. The weights are staged
+// once per CTA as stored ([out][in], K-major for the forward GEMMs); the
+// backward GEMMs read the same copy as an MN-major B operand. Rounding
+// points: features, a1, a2 and the back-propagated factors in bf16,
+// dsilu(z1), dsilu(z2) in binary16, everything else fp32.
+constexpr int TM = 128;                 // rows per tile = TMEM lanes
+constexpr int TC_THREADS = 512;         // 2 groups x 8 warps: lane quarter (warp % 4) x column half
+constexpr int TC_GROUP = 256;
+constexpr int KF1 = 80;                 // layer-1 K (67 features + zero padding to a multiple of 16)
+constexpr int TMEM_COLS = 512;          // per group (256 columns each): accumulator [0,128),
+                                        // dsilu(z1) [128,192), dsilu(z2) [192,256) (binary16 pairs)
+constexpr int SZ_W1 = HID * KF1 * 2, SZ_W = HID * HID * 2, SZ_X = TM * HID * 2;
+constexpr int O_W1 = 0, O_W2 = O_W1 + SZ_W1, O_W3 = O_W2 + SZ_W, O_X = O_W3 + SZ_W, O_F32 = O_X + 2 * SZ_X;
+// fp32 area: b1, b2, b3, w4 (bf16-rounded) [4 x 128], B [96], b4, then per
+// group the second column half's partial sums: y [128], dy/dxh [128 x 3],
+// then s * w4 [128]
+constexpr int F_BIAS = 0, F_BQ = 4 * HID, F_B4 = F_BQ + 96, F_YP = F_B4 + 4, F_GP = F_YP + 2 * TM,
+              F_SW4 = F_GP + 6 * TM, F_END = F_SW4 + HID;     // s * w4 [128] last
+constexpr int O_BAR = O_F32 + 4 * F_END;
+constexpr size_t TC_SMEM = (size_t)O_BAR + 32;    // 2 mbarriers, TMEM address, 2 wait flags
+static_assert(O_X % 1024 == 0 && O_BAR % 8 == 0 && TC_SMEM <= 232448, "tcgen05 MLP shared memory layout");
+constexpr int TC_WAIT_LIMIT = 1 << 24;  // mbarrier polls before a tile is abandoned (outputs NaN)
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p)
 {
     return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-__device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3)
+// byte offset of element (r, k) of a matrix with row extent kdim: core
+// matrices of 8 rows x 8 elements (16 bytes per row, 128 bytes each),
+// column-adjacent core matrices 128 bytes apart, row groups kdim * 16 bytes
+// apart. Read with r as M/N and k as K this is the K-major operand layout;
+// read with r as K and k as N it is the MN-major one.
+__device__ __forceinline__ int core_off(int r, int k, int kdim)
 {
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3) : "r"(addr));
+    return ((r >> 3) * (kdim >> 3) + (k >> 3)) * 128 + (r & 7) * 16 + (k & 7) * 2;
 }
 
-__device__ __forceinline__ void ldsm_x4_t(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3)
+// shared-memory matrix descriptor (no swizzle): start, leading byte offset
+// (between core matrices adjacent in K), stride byte offset (between core
+// matrices adjacent in M/N), version 1
+__device__ __forceinline__ uint64_t sm_desc(uint32_t addr, uint32_t lbo, uint32_t sbo)
 {
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3) : "r"(addr));
+    return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
 }
 
-__device__ __forceinline__ void mma(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1)
+// instruction descriptor, kind::f16: fp32 D, bf16 A and B, A K-major, B
+// K-major or MN-major, M = 128
+__device__ __forceinline__ uint32_t tc_idesc(int N, bool b_mn)
 {
-    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-                 "{%0,%1,%2,%3};\n"
-                 : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+    return (1u << 4) | (1u << 7) | (1u << 10) | (b_mn ? 1u << 16 : 0u) | ((uint32_t)(N >> 3) << 17) |
+           ((uint32_t)(TM >> 4) << 24);
 }
 
-__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
+// forward GEMM: D[128 x N] (TMEM) = X[128 x K] * W[N x K]^T, W stored [N][K]
+__device__ __forceinline__ void tc_gemm_fwd(uint32_t tmem_d, uint32_t xa, uint32_t wa, int K, int N)
 {
-    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
-    return *reinterpret_cast<uint32_t*>(&v);
-}
-
-// acc[16][4] = A[16 x 16*KSTEPS] * W^T, W [128][stride] row-major (out, in):
-// forward use, B(k = in, n = out) fragments by ldmatrix on W's rows
-template <int KSTEPS, int STRIDE>
-__device__ __forceinline__ void gemm_fwd(float (&acc)[16][4], const uint32_t (&A)[KSTEPS][4],
-                                         const __nv_bfloat16* W, int lane)
-{
-#pragma unroll
-    for (int j = 0; j < 16; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
-    const int mi = lane >> 3, ri = lane & 7;
-#pragma unroll
-    for (int kk = 0; kk < KSTEPS; ++kk) {
-#pragma unroll
-        for (int jp = 0; jp < 8; ++jp) {
-            // matrices: (n0, k0), (n0, k0+8), (n0+8, k0), (n0+8, k0+8)
-            const int n = jp * 16 + (mi >> 1) * 8 + ri;
-            const int k = kk * 16 + (mi & 1) * 8;
-            uint32_t b0, b1, b2, b3;
-            ldsm_x4(smem_addr(W + n * STRIDE + k), b0, b1, b2, b3);
-            mma(acc[2 * jp], A[kk], b0, b1);
-            mma(acc[2 * jp + 1], A[kk], b2, b3);
-        }
+    const uint32_t idesc = tc_idesc(N, false);
+    const uint32_t sbo = (uint32_t)(K / 8) * 128u;
+    for (int ks = 0; ks < K / 16; ++ks) {
+        const uint64_t da = sm_desc(xa + 256u * ks, 128u, sbo);
+        const uint64_t db = sm_desc(wa + 256u * ks, 128u, sbo);
+        const uint32_t accum = ks > 0 ? 1u : 0u;
+        asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                     "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+                     ::"r"(tmem_d), "l"(da), "l"(db), "r"(idesc), "r"(accum));
     }
 }
 
-// acc[NT][4] = G[16 x 128] * W, W [128][stride] (out, in): input-gradient use,
-// B(k = out, n = in) fragments by transposing ldmatrix on W's rows
-template <int NT, int STRIDE>
-__device__ __forceinline__ void gemm_bwd(float (&acc)[NT][4], const uint32_t (&G)[8][4], const __nv_bfloat16* W,
-                                         int lane)
+// backward GEMM: D[128 x N] = X[128 x 128] * W[128 x N], W stored [128][N]
+// (row = K): the stored copy read as an MN-major B operand
+__device__ __forceinline__ void tc_gemm_bwd(uint32_t tmem_d, uint32_t xa, uint32_t wa, int N)
 {
-#pragma unroll
-    for (int j = 0; j < NT; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
-    const int mi = lane >> 3, ri = lane & 7;
-#pragma unroll
-    for (int kk = 0; kk < 8; ++kk) {
-#pragma unroll
-        for (int jp = 0; jp < NT / 2; ++jp) {
-            // matrices: (k0, n0), (k0+8, n0), (k0, n0+8), (k0+8, n0+8)
-            const int k = kk * 16 + (mi & 1) * 8 + ri;
-            const int n = jp * 16 + (mi >> 1) * 8;
-            uint32_t b0, b1, b2, b3;
-            ldsm_x4_t(smem_addr(W + k * STRIDE + n), b0, b1, b2, b3);
-            mma(acc[2 * jp], G[kk], b0, b1);
-            mma(acc[2 * jp + 1], G[kk], b2, b3);
-        }
+    const uint32_t idesc = tc_idesc(N, true);
+    const uint32_t lbo = (uint32_t)(N / 8) * 128u;     // next 8 rows (K) of W
+    for (int ks = 0; ks < HID / 16; ++ks) {
+        const uint64_t da = sm_desc(xa + 256u * ks, 128u, (HID / 8) * 128u);
+        const uint64_t db = sm_desc(wa + 2u * lbo * ks, lbo, 128u);
+        const uint32_t accum = ks > 0 ? 1u : 0u;
+        asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                     "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+                     ::"r"(tmem_d), "l"(da), "l"(db), "r"(idesc), "r"(accum));
     }
 }
 
-// C fragments [16 x 128] -> next layer's A fragments (8 k-steps)
-__device__ __forceinline__ void c_to_a(const float (&v)[16][4], uint32_t (&A)[8][4])
+__device__ __forceinline__ void tc_commit(uint32_t bar)
 {
-#pragma unroll
-    for (int kk = 0; kk < 8; ++kk) {
-        A[kk][0] = pack_bf16(v[2 * kk][0], v[2 * kk][1]);
-        A[kk][1] = pack_bf16(v[2 * kk][2], v[2 * kk][3]);
-        A[kk][2] = pack_bf16(v[2 * kk + 1][0], v[2 * kk + 1][1]);
-        A[kk][3] = pack_bf16(v[2 * kk + 1][2], v[2 * kk + 1][3]);
-    }
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar));
 }
 
-__global__ void __launch_bounds__(IW * 32, 1) k_mlp_infer(const float* __restrict__ P, Frame fr,
+// bounded wait for the mbarrier phase with parity `ph`
+__device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t ph)
+{
+    uint32_t done = 0;
+    for (int it = 0; it < TC_WAIT_LIMIT && !done; ++it)
+        asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+                     : "=r"(done) : "r"(bar), "r"(ph));
+    return done != 0;
+}
+
+#define TC_R8(v, o) "=r"(v[o]), "=r"(v[o + 1]), "=r"(v[o + 2]), "=r"(v[o + 3]), "=r"(v[o + 4]), "=r"(v[o + 5]), \
+                    "=r"(v[o + 6]), "=r"(v[o + 7])
+#define TC_W8(v, o) "r"(v[o]), "r"(v[o + 1]), "r"(v[o + 2]), "r"(v[o + 3]), "r"(v[o + 4]), "r"(v[o + 5]), \
+                    "r"(v[o + 6]), "r"(v[o + 7])
+
+// consecutive TMEM columns of this thread's lane; tm_wait_ld completes
+// every load issued before it
+__device__ __forceinline__ void tm_ld32(uint32_t ta, uint32_t (&v)[32])
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                 "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                 : TC_R8(v, 0), TC_R8(v, 8), TC_R8(v, 16), TC_R8(v, 24) : "r"(ta));
+}
+
+__device__ __forceinline__ void tm_ld16(uint32_t ta, uint32_t (&v)[16])
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                 : TC_R8(v, 0), TC_R8(v, 8) : "r"(ta));
+}
+
+__device__ __forceinline__ void tm_ld8(uint32_t ta, uint32_t (&v)[32])
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : TC_R8(v, 0) : "r"(ta));
+}
+
+__device__ __forceinline__ void tm_wait_ld()
+{
+    asm volatile("tcgen05.wait::ld.sync.aligned;");
+}
+
+__device__ __forceinline__ void tm_st16(uint32_t ta, const uint32_t (&v)[16])
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};"
+                 ::"r"(ta), TC_W8(v, 0), TC_W8(v, 8));
+    asm volatile("tcgen05.wait::st.sync.aligned;");
+}
+
+// 8 consecutive bf16 values into one 16-byte row of a core matrix
+__device__ __forceinline__ void st_bf16x8(unsigned char* base, int off, const float* f)
+{
+    uint4 u;
+    __nv_bfloat162 p0 = __floats2bfloat162_rn(f[0], f[1]), p1 = __floats2bfloat162_rn(f[2], f[3]);
+    __nv_bfloat162 p2 = __floats2bfloat162_rn(f[4], f[5]), p3 = __floats2bfloat162_rn(f[6], f[7]);
+    u.x = *reinterpret_cast<uint32_t*>(&p0);
+    u.y = *reinterpret_cast<uint32_t*>(&p1);
+    u.z = *reinterpret_cast<uint32_t*>(&p2);
+    u.w = *reinterpret_cast<uint32_t*>(&p3);
+    *reinterpret_cast<uint4*>(base + off) = u;
+}
+
+// sin(pi p), cos(pi p): p reduced exactly to [-1, 1] (p - 2 rint(p / 2)),
+// then the hardware sine and cosine on [-pi, pi] (absolute error about
+// 2^-21, far below the bfloat16 rounding of the features)
+__device__ __forceinline__ void sincospi_tc(float p, float* sv, float* cv)
+{
+    const float rr = p - 2.f * rintf(0.5f * p);
+    __sincosf(3.14159265358979f * rr, sv, cv);
+}
+
+// silu(z) and dsilu(z) from one logistic sigmoid (approximate reciprocal:
+// relative error ~1e-7, far below the bfloat16 rounding that follows)
+__device__ __forceinline__ void silu_pair(float z, float& a, float& da)
+{
+    const float sg = __fdividef(1.f, 1.f + __expf(-z));
+    a = z * sg;
+    da = sg * fmaf(z, 1.f - sg, 1.f);
+}
+
+// the group's named barrier (ids 1, 2; 256 threads)
+__device__ __forceinline__ void group_sync(int g)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "r"(TC_GROUP));
+}
+
+__device__ __forceinline__ bool group_all(int g, bool p)
+{
+    uint32_t r;
+    asm volatile("{\n.reg .pred q, o;\nsetp.ne.u32 q, %1, 0;\nbar.red.and.pred o, %2, %3, q;\nselp.u32 %0, 1, 0, o;\n}\n"
+                 : "=r"(r) : "r"((uint32_t)p), "r"(1 + g), "r"(TC_GROUP));
+    return r != 0;
+}
+
+// make this thread's shared-memory and TMEM writes visible to the next
+// tensor-core operation of the group, then hand the issue to its thread 0
+__device__ __forceinline__ void tc_sync_before_mma(int g)
+{
+    asm volatile("fence.proxy.async.shared::cta;");
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    group_sync(g);
+    asm volatile("tcgen05.fence::after_thread_sync;");
+}
+
+// wait for the group's GEMMs: its issuing thread polls the mbarrier, the
+// other threads sleep in the group barrier (no issue slots taken from the
+// other group); returns whether the GEMMs completed
+__device__ __forceinline__ bool group_wait(int g, bool issuer, uint32_t bar, uint32_t ph, volatile int* flag)
+{
+    if (issuer) *flag = bar_wait(bar, ph) ? 1 : 0;
+    group_sync(g);
+    const bool ok = *flag != 0;
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    return ok;
+}
+
+__device__ __forceinline__ uint32_t pack_h2(float lo, float hi)
+{
+    __half2 h = __floats2half2_rn(lo, hi);
+    return *reinterpret_cast<uint32_t*>(&h);
+}
+
+__global__ void __launch_bounds__(TC_THREADS, 1) k_mlp_tc(const float* __restrict__ P, Frame fr,
                                                           const float* __restrict__ x, int n,
                                                           float* __restrict__ y, float* __restrict__ dydx)
 {
-    extern __shared__ __align__(16) unsigned char smem[];
-    __nv_bfloat16* W1 = reinterpret_cast<__nv_bfloat16*>(smem);
-    __nv_bfloat16* W2 = W1 + HID * S1;
-    __nv_bfloat16* W3 = W2 + HID * S2;
-    float* bias = reinterpret_cast<float*>(W3 + HID * S2);   // b1, b2, b3, w4 (bf16-rounded)
-    float* Bq = bias + 4 * HID;                               // frequencies [32][3]
-    float* misc = Bq + 96;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    float* Fw = misc + 8 + warp * (16 * FS);
-    __half* stash = reinterpret_cast<__half*>(misc + 8 + IW * 16 * FS) + warp * SMEM_STASH;
-    // stage the weights (rounded to bf16) once per block
-    for (int i = tid; i < HID * S1; i += blockDim.x) {
-        int o = i / S1, k = i - o * S1;
-        W1[i] = __float2bfloat16_rn(k < NIN ? P[OFF_W1 + o * NIN + k] : 0.f);
+    extern __shared__ __align__(1024) unsigned char smem[];
+    float* F32 = reinterpret_cast<float*>(smem + O_F32);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + O_BAR + 16);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int g = warp >> 3, gw = warp & 7, gt = tid & (TC_GROUP - 1);
+    const int row = (gw & 3) * 32 + lane, half = gw >> 2;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     ::"r"(smem_addr(tmem_slot)), "r"(TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
-    for (int i = tid; i < HID * S2; i += blockDim.x) {
-        int o = i / S2, k = i - o * S2;
-        W2[i] = __float2bfloat16_rn(k < HID ? P[OFF_W2 + o * HID + k] : 0.f);
-        W3[i] = __float2bfloat16_rn(k < HID ? P[OFF_W3 + o * HID + k] : 0.f);
+    if (tid < 2) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(smem + O_BAR + 8 * tid)), "r"(1));
+        asm volatile("fence.mbarrier_init.release.cluster;");
     }
-    for (int i = tid; i < HID; i += blockDim.x) {
-        bias[i] = P[OFF_B1 + i];
-        bias[HID + i] = P[OFF_B2 + i];
-        bias[2 * HID + i] = P[OFF_B3 + i];
-        bias[3 * HID + i] = bf16r(P[OFF_W4 + i]);
+    // the weights in bf16 as stored, [out][in]
+    for (int i = tid; i < HID * KF1; i += TC_THREADS) {
+        const int o = i / KF1, k = i - o * KF1;
+        *reinterpret_cast<__nv_bfloat16*>(smem + O_W1 + core_off(o, k, KF1)) =
+            __float2bfloat16_rn(k < NIN ? P[OFF_W1 + o * NIN + k] : 0.f);
     }
-    for (int i = tid; i < 96; i += blockDim.x) Bq[i] = P[OFF_B + i];
-    if (tid == 0) misc[0] = P[OFF_B4];
+    for (int i = tid; i < HID * HID; i += TC_THREADS) {
+        const int o = i / HID, k = i - o * HID;
+        *reinterpret_cast<__nv_bfloat16*>(smem + O_W2 + core_off(o, k, HID)) = __float2bfloat16_rn(P[OFF_W2 + i]);
+        *reinterpret_cast<__nv_bfloat16*>(smem + O_W3 + core_off(o, k, HID)) = __float2bfloat16_rn(P[OFF_W3 + i]);
+    }
+    for (int i = tid; i < HID; i += TC_THREADS) {
+        F32[F_BIAS + i] = P[OFF_B1 + i];
+        F32[F_BIAS + HID + i] = P[OFF_B2 + i];
+        F32[F_BIAS + 2 * HID + i] = P[OFF_B3 + i];
+        F32[F_BIAS + 3 * HID + i] = bf16r(P[OFF_W4 + i]);
+        F32[F_SW4 + i] = fr.s * bf16r(P[OFF_W4 + i]);
+    }
+    for (int i = tid; i < 96; i += TC_THREADS) F32[F_BQ + i] = P[OFF_B + i];
+    if (tid == 0) F32[F_B4] = P[OFF_B4];
+    asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
-    const int g = lane >> 2, t4 = lane & 3;
-    const int ntiles = (n + 15) / 16;
-    for (int tile = blockIdx.x * IW + warp; tile < ntiles; tile += gridDim.x * IW) {
-        const int r0 = tile * 16;
-        // features of the 16 rows: lanes 0..15 write xh, every lane 16 projections
-        {
-            const int row = lane >> 1, half = lane & 1;
-            const int gr = min(r0 + row, n - 1);
-            float xh[3];
-            for (int j = 0; j < 3; ++j) xh[j] = (x[3 * gr + j] - fr.c[j]) / fr.h[j];
-            float* f = Fw + row * FS;
-            if (!half) { f[0] = xh[0]; f[1] = xh[1]; f[2] = xh[2]; }
-            for (int mm = 0; mm < 16; ++mm) {
-                const int m = half * 16 + mm;
-                float p = fmaf(Bq[3 * m], xh[0], fmaf(Bq[3 * m + 1], xh[1], Bq[3 * m + 2] * xh[2]));
-                float sv, cv;
-                sincospif(p, &sv, &cv);
-                f[3 + m] = sv;
-                f[3 + NF + m] = cv;
-            }
-            if (!half) for (int c = NIN; c < 80; ++c) f[c] = 0.f;
-        }
-        __syncwarp();
-        uint32_t A1[5][4];
-#pragma unroll
-        for (int kk = 0; kk < 5; ++kk) {
-            const int c = kk * 16 + 2 * t4;
-            A1[kk][0] = pack_bf16(Fw[g * FS + c], Fw[g * FS + c + 1]);
-            A1[kk][1] = pack_bf16(Fw[(g + 8) * FS + c], Fw[(g + 8) * FS + c + 1]);
-            A1[kk][2] = pack_bf16(Fw[g * FS + c + 8], Fw[g * FS + c + 9]);
-            A1[kk][3] = pack_bf16(Fw[(g + 8) * FS + c + 8], Fw[(g + 8) * FS + c + 9]);
-        }
-        float acc[16][4];
-        uint32_t A[8][4];
-        uint32_t G[8][4];
-        const float* w4 = bias + 3 * HID;
-        // hidden layers 1, 2: z = acc + b, stash dsilu(z), a = silu(z)
-        gemm_fwd<5, S1>(acc, A1, W1, lane);
-#pragma unroll
-        for (int layer = 0; layer < 2; ++layer) {
-            if (layer == 1) gemm_fwd<8, S2>(acc, A, W2, lane);
-            const float* b = bias + layer * HID;
-            __half* st = stash + layer * 16 * HID;
-#pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                const int c = 8 * j + 2 * t4;
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const int row = g + (e >> 1) * 8, col = c + (e & 1);
-                    const float z = acc[j][e] + b[col];
-                    st[row * HID + col] = __float2half_rn(dsilu(z));
-                    acc[j][e] = silu(z);
-                }
-            }
-            c_to_a(acc, A);
-        }
-        // layer 3: a3 stays in acc; the input gradient starts from
-        // g3 = s w4 dsilu(z3), packed straight into A fragments
-        gemm_fwd<8, S2>(acc, A, W3, lane);
-#pragma unroll
-        for (int kk = 0; kk < 8; ++kk) {
-            float gv[2][4];
-#pragma unroll
-            for (int h2 = 0; h2 < 2; ++h2) {
-                const int j = 2 * kk + h2;
-                const int c = 8 * j + 2 * t4;
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const int col = c + (e & 1);
-                    const float z = acc[j][e] + bias[2 * HID + col];
-                    gv[h2][e] = fr.s * w4[col] * dsilu(z);
-                    acc[j][e] = silu(z);
-                }
-            }
-            G[kk][0] = pack_bf16(gv[0][0], gv[0][1]);
-            G[kk][1] = pack_bf16(gv[0][2], gv[0][3]);
-            G[kk][2] = pack_bf16(gv[1][0], gv[1][1]);
-            G[kk][3] = pack_bf16(gv[1][2], gv[1][3]);
-        }
-        // output: y = s (w4 . a3 + b4), rows g and g + 8
-        float ya = 0.f, yb = 0.f;
-#pragma unroll
-        for (int j = 0; j < 16; ++j) {
-            const int c = 8 * j + 2 * t4;
-            ya = fmaf(acc[j][0], w4[c], fmaf(acc[j][1], w4[c + 1], ya));
-            yb = fmaf(acc[j][2], w4[c], fmaf(acc[j][3], w4[c + 1], yb));
-        }
-        ya += __shfl_xor_sync(0xffffffffu, ya, 1);
-        ya += __shfl_xor_sync(0xffffffffu, ya, 2);
-        yb += __shfl_xor_sync(0xffffffffu, yb, 1);
-        yb += __shfl_xor_sync(0xffffffffu, yb, 2);
-        if (t4 == 0) {
-            if (r0 + g < n) y[r0 + g] = fr.s * (ya + misc[0]);
-            if (r0 + g + 8 < n) y[r0 + g + 8] = fr.s * (yb + misc[0]);
-        }
-        __syncwarp();
-        if (dydx) {
-            // back through W3, W2 (times the stashed dsilu), W1
-#pragma unroll
-            for (int layer = 1; layer >= 0; --layer) {
-                gemm_bwd<16, S2>(acc, G, layer == 1 ? W3 : W2, lane);
-                const __half* st = stash + layer * 16 * HID;
-#pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const int c = 8 * j + 2 * t4;
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const int row = g + (e >> 1) * 8, col = c + (e & 1);
-                        acc[j][e] *= __half2float(st[row * HID + col]);
-                    }
-                }
-                c_to_a(acc, G);
-            }
-            float gf[10][4];
-            gemm_bwd<10, S1>(gf, G, W1, lane);
-            // features -> xh: d f_j / d xh for xh, sin(pi B xh), cos(pi B xh)
-            float ga[3] = {0.f, 0.f, 0.f}, gb[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-            for (int j = 0; j < 10; ++j) {
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const int row = g + (e >> 1) * 8, col = 8 * j + 2 * t4 + (e & 1);
-                    const float v = gf[j][e];
-                    float* gg = (e >> 1) ? gb : ga;
-                    if (col < 3) {
-                        gg[col] += v;
-                    } else if (col < 3 + NF) {
-                        const int m = col - 3;
-                        const float k = v * 3.14159265358979f * Fw[row * FS + 3 + NF + m];
-                        gg[0] = fmaf(k, Bq[3 * m], gg[0]); gg[1] = fmaf(k, Bq[3 * m + 1], gg[1]);
-                        gg[2] = fmaf(k, Bq[3 * m + 2], gg[2]);
-                    } else if (col < NIN) {
-                        const int m = col - 3 - NF;
-                        const float k = -v * 3.14159265358979f * Fw[row * FS + 3 + m];
-                        gg[0] = fmaf(k, Bq[3 * m], gg[0]); gg[1] = fmaf(k, Bq[3 * m + 1], gg[1]);
-                        gg[2] = fmaf(k, Bq[3 * m + 2], gg[2]);
-                    }
-                }
-            }
-#pragma unroll
-            for (int j = 0; j < 3; ++j) {
-                ga[j] += __shfl_xor_sync(0xffffffffu, ga[j], 1);
-                ga[j] += __shfl_xor_sync(0xffffffffu, ga[j], 2);
-                gb[j] += __shfl_xor_sync(0xffffffffu, gb[j], 1);
-                gb[j] += __shfl_xor_sync(0xffffffffu, gb[j], 2);
-            }
-            if (t4 == 0) {
-                if (r0 + g < n)
-                    for (int j = 0; j < 3; ++j) dydx[3 * (r0 + g) + j] = ga[j] / fr.h[j];
-                if (r0 + g + 8 < n)
-                    for (int j = 0; j < 3; ++j) dydx[3 * (r0 + g + 8) + j] = gb[j] / fr.h[j];
-            }
-        }
-        __syncwarp();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    // this group's accumulator columns and this warp's lane quarter
+    const uint32_t tg = *tmem_slot + (uint32_t)(g * 256);
+    const uint32_t tl = tg + ((uint32_t)((gw & 3) * 32) << 16);
+    const uint32_t bar_a = smem_addr(smem + O_BAR + 8 * g), xa = smem_addr(smem + O_X + g * SZ_X);
+    const uint32_t w1a = smem_addr(smem + O_W1), w2a = smem_addr(smem + O_W2), w3a = smem_addr(smem + O_W3);
+    unsigned char* X = smem + O_X + g * SZ_X;
+    const float* w4 = F32 + F_BIAS + 3 * HID;
+    const float* Bq = F32 + F_BQ;
+    float* yp_h = F32 + F_YP + g * TM;          // the second half's partial y
+    float* gp_h = F32 + F_GP + g * 3 * TM;      // and partial dy/dxh
+    const bool issuer = gt == 0;
+    volatile int* wflag = reinterpret_cast<volatile int*>(smem + O_BAR + 24 + 4 * g);
+    uint32_t ph = 0;
+    const int ntiles = (n + TM - 1) / TM;
+    const int t0 = 2 * (int)blockIdx.x + g, tstep = 2 * (int)gridDim.x;
+    float xn[3] = {0.f, 0.f, 0.f};
+    if (t0 < ntiles) {
+        const int gr = min(t0 * TM + row, n - 1);
+        for (int j = 0; j < 3; ++j) xn[j] = x[3 * gr + j];
     }
+    for (int tile = t0; tile < ntiles; tile += tstep) {
+        const int r = tile * TM + row;
+        float xh[3];
+        for (int j = 0; j < 3; ++j) xh[j] = (xn[j] - fr.c[j]) / fr.h[j];
+        if (tile + tstep < ntiles) {                    // the next tile's query, early
+            const int gr = min((tile + tstep) * TM + row, n - 1);
+            for (int j = 0; j < 3; ++j) xn[j] = x[3 * gr + j];
+        }
+        // features: this half's 40 columns of [xh, sin(pi B xh), cos(pi B xh), 0...]
+#pragma unroll 1
+        for (int fc = 0; fc < 5; ++fc) {
+            float f[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int c = half * 40 + fc * 8 + j;
+                float v = 0.f;
+                if (c < 3) {
+                    v = xh[c];
+                } else if (c < NIN) {
+                    const int m = c < 3 + NF ? c - 3 : c - 3 - NF;
+                    const float pp = fmaf(Bq[3 * m], xh[0], fmaf(Bq[3 * m + 1], xh[1], Bq[3 * m + 2] * xh[2]));
+                    float sv, cv;
+                    sincospi_tc(pp, &sv, &cv);
+                    v = c < 3 + NF ? sv : cv;
+                }
+                f[j] = v;
+            }
+            st_bf16x8(X, core_off(row, half * 40 + fc * 8, KF1), f);
+        }
+        bool ok = true;
+        // forward: layers 1..3
+#pragma unroll 1
+        for (int layer = 0; layer < 3; ++layer) {
+            tc_sync_before_mma(g);
+            if (issuer) {
+                if (layer == 0) tc_gemm_fwd(tg, xa, w1a, KF1, HID);
+                else tc_gemm_fwd(tg, xa, layer == 1 ? w2a : w3a, HID, HID);
+                tc_commit(bar_a);
+            }
+            ok = group_wait(g, issuer, bar_a, ph, wflag) && ok;
+            ph ^= 1u;
+            const float4* bb = reinterpret_cast<const float4*>(F32 + F_BIAS + layer * HID);
+            const float4* w4v = reinterpret_cast<const float4*>(w4);
+            const float4* sw4v = reinterpret_cast<const float4*>(F32 + F_SW4);
+            float yp = 0.f;
+#pragma unroll 1
+            for (int cc = 0; cc < 2; ++cc) {
+                const int c0 = half * 64 + cc * 32;
+                uint32_t v[32];
+                tm_ld32(tl + c0, v);
+                tm_wait_ld();
+                float a[32];
+                uint32_t hp[16];
+#pragma unroll
+                for (int j = 0; j < 32; j += 4) {
+                    const float4 b4 = bb[(c0 + j) >> 2];
+                    const float bz[4] = {b4.x, b4.y, b4.z, b4.w};
+                    float sz[4], dz[4];
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) silu_pair(__uint_as_float(v[j + e]) + bz[e], sz[e], dz[e]);
+                    if (layer < 2) {
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) a[j + e] = sz[e];
+                        hp[j >> 1] = pack_h2(dz[0], dz[1]);
+                        hp[(j >> 1) + 1] = pack_h2(dz[2], dz[3]);
+                    } else {
+                        // layer 3: y partial from a3, the backward pass starts
+                        // from g3 = s w4 dsilu(z3)
+                        const float4 w = w4v[(c0 + j) >> 2], sw = sw4v[(c0 + j) >> 2];
+                        yp = fmaf(sz[0], w.x, fmaf(sz[1], w.y, fmaf(sz[2], w.z, fmaf(sz[3], w.w, yp))));
+                        a[j] = sw.x * dz[0];
+                        a[j + 1] = sw.y * dz[1];
+                        a[j + 2] = sw.z * dz[2];
+                        a[j + 3] = sw.w * dz[3];
+                    }
+                }
+                if (layer < 2) tm_st16(tl + (uint32_t)(HID + layer * 64 + (c0 >> 1)), hp);
+#pragma unroll
+                for (int kb = 0; kb < 4; ++kb) st_bf16x8(X, core_off(row, c0 + kb * 8, HID), a + 8 * kb);
+            }
+            if (layer == 2) {
+                if (half) yp_h[row] = yp;
+                group_sync(g);
+                if (!half && r < n) y[r] = ok ? fr.s * ((yp + yp_h[row]) + F32[F_B4]) : __int_as_float(0x7fffffff);
+            }
+        }
+        if (dydx) {
+            // backward: g2 = (g3 W3) dsilu(z2), g1 = (g2 W2) dsilu(z1), gf = g1 W1
+#pragma unroll 1
+            for (int layer = 2; layer >= 0; --layer) {
+                tc_sync_before_mma(g);
+                if (issuer) {
+                    if (layer == 0) tc_gemm_bwd(tg, xa, w1a, KF1);
+                    else tc_gemm_bwd(tg, xa, layer == 2 ? w3a : w2a, HID);
+                    tc_commit(bar_a);
+                }
+                ok = group_wait(g, issuer, bar_a, ph, wflag) && ok;
+                ph ^= 1u;
+                if (layer > 0) {
+#pragma unroll 1
+                    for (int cc = 0; cc < 2; ++cc) {
+                        const int c0 = half * 64 + cc * 32;
+                        uint32_t v[32], d[16];
+                        tm_ld32(tl + c0, v);
+                        tm_ld16(tl + (uint32_t)(HID + (layer - 1) * 64 + (c0 >> 1)), d);
+                        tm_wait_ld();
+                        float a[32];
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) {
+                            const float2 dd = __half22float2(*reinterpret_cast<const __half2*>(&d[j]));
+                            a[2 * j] = __uint_as_float(v[2 * j]) * dd.x;
+                            a[2 * j + 1] = __uint_as_float(v[2 * j + 1]) * dd.y;
+                        }
+#pragma unroll
+                        for (int kb = 0; kb < 4; ++kb) st_bf16x8(X, core_off(row, c0 + kb * 8, HID), a + 8 * kb);
+                    }
+                } else {
+                    // features -> xh: columns [40 half, 40 half + 40) of gf
+                    float gg[3] = {0.f, 0.f, 0.f};
+#pragma unroll 1
+                    for (int cc = 0; cc < 2; ++cc) {
+                        const int c0 = half * 40 + cc * 32;
+                        uint32_t v[32];
+                        if (cc == 0) tm_ld32(tl + c0, v);
+                        else tm_ld8(tl + c0, v);
+                        tm_wait_ld();
+                        const int cn = cc == 0 ? 32 : 8;
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) {
+                            if (j >= cn) break;
+                            const int c = c0 + j;
+                            const float gv = __uint_as_float(v[j]);
+                            if (c < 3) {
+                                gg[c] += gv;
+                            } else if (c < NIN) {
+                                const int m = c < 3 + NF ? c - 3 : c - 3 - NF;
+                                const float pp =
+                                    fmaf(Bq[3 * m], xh[0], fmaf(Bq[3 * m + 1], xh[1], Bq[3 * m + 2] * xh[2]));
+                                float sv, cv;
+                                sincospi_tc(pp, &sv, &cv);
+                                const float k = c < 3 + NF ? gv * 3.14159265358979f * cv
+                                                           : -gv * 3.14159265358979f * sv;
+                                gg[0] = fmaf(k, Bq[3 * m], gg[0]);
+                                gg[1] = fmaf(k, Bq[3 * m + 1], gg[1]);
+                                gg[2] = fmaf(k, Bq[3 * m + 2], gg[2]);
+                            }
+                        }
+                    }
+                    if (half)
+                        for (int j = 0; j < 3; ++j) gp_h[3 * row + j] = gg[j];
+                    group_sync(g);
+                    if (!half && r < n)
+                        for (int j = 0; j < 3; ++j)
+                            dydx[3 * r + j] = ok ? (gg[j] + gp_h[3 * row + j]) / fr.h[j] : __int_as_float(0x7fffffff);
+                }
+            }
+        }
+        // a tile whose tensor-core work did not complete ends the group's walk
+        if (!group_all(g, ok)) break;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(*tmem_slot), "r"(TMEM_COLS));
 }
 
 int sm_count_mlp()
@@ -541,11 +703,11 @@ extern "C" int sd_mlp_forward(const float* params, const float* frame, const flo
     if (!params || !frame || !frame_ok(frame) || n < 0 || (n > 0 && (!x || !y))) return SD_ERR_INVALID_ARG;
     if (n == 0) return SD_OK;
     if (n >= ((int64_t)1 << 31) / 3) return SD_ERR_TOO_LARGE;
-    cudaFuncSetAttribute(k_mlp_infer, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
+    cudaFuncSetAttribute(k_mlp_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
     Frame fr = make_frame(frame);
-    int tiles = (int)((n + 15) / 16);
-    int blocks = std::max(1, std::min(sm_count_mlp(), (tiles + IW - 1) / IW));
-    k_mlp_infer<<<blocks, IW * 32, SMEM_BYTES, (cudaStream_t)stream>>>(params, fr, x, (int)n, y, dydx);
+    const int tiles = (int)((n + TM - 1) / TM);
+    const int blocks = std::max(1, std::min(sm_count_mlp(), (tiles + 1) / 2));
+    k_mlp_tc<<<blocks, TC_THREADS, TC_SMEM, (cudaStream_t)stream>>>(params, fr, x, (int)n, y, dydx);
     sd_count_launches(1);
     return sd_cuda_status(cudaGetLastError());
 }
