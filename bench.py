@@ -96,7 +96,8 @@ def _config(args, n):
     return {"workload": f"icosphere-L6 81920 tris, {args.queries} queries/GPU (70% shell, 30% box), "
                         f"alpha={args.alpha:g}, beta={args.beta:g}, leaf={args.leaf_size}",
             "triangles": 81920, "queries_per_gpu": args.queries, "alpha": args.alpha, "beta": args.beta,
-            "leaf_size": args.leaf_size, "step": "sd_build + sd_query_order + sd_query (value+grad)",
+            "leaf_size": args.leaf_size,
+            "step": "sd_build + sd_query_order (second stream, from the scene box on) + sd_query (value+grad)",
             "l2": "flushed (256 MiB write) before each timed step", "parallelism": f"replicated tree, dp{n}"}
 
 
@@ -235,15 +236,24 @@ def run_ours(args):
     grad = torch.empty(M, 3, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
+    side = torch.cuda.Stream(device=dev)
+    fork, join = torch.cuda.Event(), torch.cuda.Event()
+    order = torch.empty(M, dtype=torch.int32, device=dev)
 
     def step(evs=None):
         if evs:
             evs[0].record(stream)
+        fork.record(stream)
         # the build's input checks run on the device and are read back once
         # after the timed region (status below) instead of stalling each step
         sd = SmoothDistance(tris=(V, F), alpha=args.alpha, beta=args.beta, leaf_size=args.leaf_size, device=dev,
                             check=False)
-        order = sd.query_order(q)
+        # the query order on a second stream: it waits for the build's scene
+        # box only and overlaps the rest of the build
+        side.wait_event(fork)
+        sd.query_order(q, stream=side, out=order)
+        join.record(side)
+        stream.wait_event(join)
         if evs:
             evs[1].record(stream)
         sd.query(q, out=(val, grad), order=order)
@@ -347,13 +357,25 @@ def _extras(args, c, V, F, q, dev, M):
     dV, dF, dq = torch.empty_like(V), torch.empty_like(F), torch.empty_like(q)
     dv, dg = torch.empty(M, device=dev), torch.empty(M, 3, device=dev)
 
+    side = torch.cuda.Stream(device=dev)
+    fork, join = torch.cuda.Event(), torch.cuda.Event()
+    de = torch.empty(M, dtype=torch.int32, device=dev)
+
     def e2e_step():
+        # mesh upload and build on the main stream; query upload and order on
+        # a second one (from the build's scene box on); then the query
+        fork.record(stream)
         dV.copy_(hV, non_blocking=True)
         dF.copy_(hF, non_blocking=True)
-        dq.copy_(hq, non_blocking=True)
         s = SmoothDistance(tris=(dV, dF), alpha=args.alpha, beta=args.beta, leaf_size=args.leaf_size, device=dev,
                            check=False)
-        s.query(dq, out=(dv, dg))
+        side.wait_event(fork)
+        with torch.cuda.stream(side):
+            dq.copy_(hq, non_blocking=True)
+        s.query_order(dq, stream=side, out=de)
+        join.record(side)
+        stream.wait_event(join)
+        s.query(dq, out=(dv, dg), order=de)
         hv.copy_(dv, non_blocking=True)
         hg.copy_(dg, non_blocking=True)
 

@@ -119,7 +119,11 @@ int sd_query(const sd_tree* t, const float* q, int64_t M, float* value, float* g
  * Traversal order for sd_query: writes to `order` (device [M] int32) the
  * query indices sorted by the 24-bit Hilbert index of each query relative to
  * the tree's scene box (stable; ties keep index order). Asynchronous on
- * `stream`; uses stream-ordered temporary device memory.
+ * `stream`; uses stream-ordered temporary device memory. For a tree built
+ * with defer_checks, `stream` first waits (outside stream capture) for the
+ * point of the build at which the scene box is final, so the order may be
+ * computed on another stream than the build's, overlapping the rest of the
+ * build; the queries themselves must be ready on `stream`.
  */
 int sd_query_order(const sd_tree* t, const float* q, int64_t M, int32_t* order, void* stream);
 

@@ -424,11 +424,11 @@ __global__ void k_super_root(SdNode* nodes, float2* nw2, int nb)
 // the tree's scalars from the build's atomics (one thread): weight scales,
 // scene box for query codes, and the validation bits folded into the
 // tree's status word
-__global__ void k_finalize(const BuildScalars* bs, int n, int unit, SdScalars* sc, int* status)
+// the scene box into the tree's scalars, as soon as validation has reduced
+// it (the query order needs nothing else of the tree)
+__global__ void k_box(const BuildScalars* bs, int n, SdScalars* sc)
 {
     if (threadIdx.x || blockIdx.x) return;
-    sc->A_E = unit ? 1.f : (float)bs->A_E;
-    sc->A_T = unit ? 1.f : (float)bs->A_T;
     for (int j = 0; j < 3; ++j) {
         float lo = n ? key2f(bs->box[j]) : 0.f, hi = n ? key2f(bs->box[3 + j]) : 0.f;
         float ex = hi - lo;
@@ -436,6 +436,13 @@ __global__ void k_finalize(const BuildScalars* bs, int n, int unit, SdScalars* s
         sc->hi[j] = hi;
         sc->inv_ex[j] = ex > 0.f ? 1.f / ex : 0.f;
     }
+}
+
+__global__ void k_finalize(const BuildScalars* bs, int unit, SdScalars* sc, int* status)
+{
+    if (threadIdx.x || blockIdx.x) return;
+    sc->A_E = unit ? 1.f : (float)bs->A_E;
+    sc->A_T = unit ? 1.f : (float)bs->A_T;
     sc->status = bs->status;
     if (bs->status & ST_INDEX) atomicOr(status, 1 << SD_ERR_INDEX);
     if (bs->status & ST_TIMEOUT) atomicOr(status, 1 << SD_ERR_TIMEOUT);
@@ -672,6 +679,20 @@ extern "C" int sd_build(const sd_geometry* g, float alpha, float beta, const sd_
         int64_t most = std::max<int64_t>({geo.np, geo.nev, geo.ntv, 2 * (int64_t)geo.ne, 3 * (int64_t)geo.nf, 1});
         ++nl;
         k_validate<<<dim3(std::min(nblk(most, T), 1024), 5), T, 0, st>>>(geo, bs);
+        ++nl;
+        k_box<<<1, 32, 0, st>>>(bs, n, t->sc);
+        // with deferred checks the build returns at once: mark the point
+        // after which the scene box is final (sd_query_order waits for it,
+        // not for the whole build)
+        if (opts.defer_checks) {
+            ce = cudaEventCreateWithFlags(&t->box_ready, cudaEventDisableTiming);
+            if (ce == cudaSuccess) ce = cudaEventRecord(t->box_ready, st);
+            if (ce != cudaSuccess) {
+                if (t->box_ready) cudaEventDestroy(t->box_ready);
+                t->box_ready = nullptr;
+                cudaGetLastError();
+            }
+        }
     }
     // validation results are read once, at the end of the build; the kernels
     // below clamp every index they dereference
@@ -716,7 +737,7 @@ extern "C" int sd_build(const sd_geometry* g, float alpha, float beta, const sd_
         k_gather<<<nblk(n, T), T, 0, st>>>(geo, sv, t->params, t->hdr, t->ext, t->sorted);
     }
     ++nl;
-    k_finalize<<<1, 32, 0, st>>>(bs, n, t->weights_unit, t->sc, t->status);
+    k_finalize<<<1, 32, 0, st>>>(bs, t->weights_unit, t->sc, t->status);
     cudaFreeAsync(tmp, st);
     sd_count_launches(nl);
 
@@ -734,6 +755,7 @@ extern "C" int sd_build(const sd_geometry* g, float alpha, float beta, const sd_
         if (ce != cudaSuccess) {
             cudaStreamSynchronize(st);
             if (t->built) cudaEventDestroy(t->built);
+            if (t->box_ready) cudaEventDestroy(t->box_ready);
             cudaFreeAsync(t->mem, st);
             delete t;
             return sd_cuda_status(ce);
@@ -761,6 +783,7 @@ extern "C" int sd_build(const sd_geometry* g, float alpha, float beta, const sd_
     if (wrc != SD_OK) {
         cudaStreamSynchronize(st);
         if (t->built) cudaEventDestroy(t->built);
+        if (t->box_ready) cudaEventDestroy(t->box_ready);
         cudaFreeAsync(t->mem, st);
         delete t;
         return wrc;
@@ -851,6 +874,7 @@ extern "C" void sd_free(sd_tree* t)
         cudaEventSynchronize(t->built);
         cudaEventDestroy(t->built);
     }
+    if (t->box_ready) cudaEventDestroy(t->box_ready);
     if (t->mem) cudaFree(t->mem);
     delete t;
 }

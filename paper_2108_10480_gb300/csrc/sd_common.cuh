@@ -98,6 +98,7 @@ struct sd_tree {
     SdScalars* sc;        // device scalars written at the end of the build
     bool info_ready;      // info's device-derived fields (A, w_far, scene box) filled in
     cudaEvent_t built;    // recorded after the build's last kernel (deferred checks)
+    cudaEvent_t box_ready;   // recorded once the scene box in sc is final (deferred checks)
     // streams that have enqueued work on the tree and an event recorded after
     // their latest such work: sd_free waits for these before releasing memory
     cudaStream_t use_stream[4];

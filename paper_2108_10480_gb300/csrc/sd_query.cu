@@ -575,6 +575,15 @@ extern "C" int sd_query_order(const sd_tree* t, const float* q, int64_t M, int32
     SdUse use_{t, (cudaStream_t)stream};
     if (M == 0) return SD_OK;
     cudaStream_t st = (cudaStream_t)stream;
+    // after a deferred-check build the order needs only the scene box: wait
+    // for that point of the build (a no-op on the build's own stream), so
+    // that on another stream the order overlaps the rest of the build
+    if (t->box_ready) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone)
+            cudaStreamWaitEvent(st, t->box_ready, 0);
+        cudaGetLastError();
+    }
     int m = (int)M;
     if (m == 1) {
         int zero = 0;

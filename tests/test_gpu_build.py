@@ -88,6 +88,30 @@ def test_single_primitive_and_empty():
     assert torch.isinf(v).all() and (gr == 0).all()
 
 
+def test_order_on_a_second_stream():
+    """After a deferred-check build, sd_query_order on another stream waits
+    for the build's scene box only; joined back, the query gives exactly the
+    single-stream results."""
+    V, F = synth.icosphere(4)
+    q = torch.from_numpy(synth.shell_queries(50000, seed=5)).cuda()
+    a = _gpu(tris=(V, F), alpha=200.0, beta=0.5, check=False)
+    oa = a.query_order(q)
+    va, ga = a.query(q, order=oa)
+    main = torch.cuda.current_stream()
+    side = torch.cuda.Stream()
+    fork, join = torch.cuda.Event(), torch.cuda.Event()
+    for _ in range(3):
+        fork.record(main)
+        b = _gpu(tris=(V, F), alpha=200.0, beta=0.5, check=False)
+        side.wait_event(fork)
+        ob = b.query_order(q, stream=side)
+        join.record(side)
+        main.wait_event(join)
+        vb, gb = b.query(q, order=ob)
+        assert torch.equal(oa, ob) and torch.equal(va, vb) and torch.equal(ga, gb)
+        assert b.status() == 0
+
+
 def test_deferred_checks():
     """check=False enqueues the same build without waiting: identical tree,
     identical query results, and invalid input reported by status()."""
