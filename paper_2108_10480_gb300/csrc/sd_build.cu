@@ -495,6 +495,27 @@ size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
 }  // namespace
 
+// One library-owned non-blocking stream per device for the build's
+// independent branch (weight parameters and the leaf-order gather run there
+// beside the Morton sort, the topology and the aggregates).
+static std::mutex g_side_mu;
+static cudaStream_t g_side[64] = {};
+
+static cudaStream_t side_stream(int dev)
+{
+    if (dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> g(g_side_mu);
+    if (!g_side[dev]) {
+        cudaStream_t s = nullptr;
+        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        g_side[dev] = s;
+    }
+    return g_side[dev];
+}
+
 static std::mutex g_use_mu;
 
 void sd_mark_use(const sd_tree* tc, cudaStream_t st)
@@ -697,22 +718,42 @@ extern "C" int sd_build(const sd_geometry* g, float alpha, float beta, const sd_
     // validation results are read once, at the end of the build; the kernels
     // below clamp every index they dereference
 
+    // The weight parameters (incidence counts, App. C.2-C.3) do not feed the
+    // Morton codes, the sort or the topology: they run on the side stream
+    // from here on, and the leaf-order gather follows them there once the
+    // sort is done; the aggregates (which need A) and the end of the build
+    // wait for them. Without a side stream everything stays on `st`.
+    cudaStream_t ps = st;
+    cudaEvent_t ev_fork = nullptr, ev_params = nullptr, ev_sorted = nullptr, ev_gather = nullptr;
+    if (n > 0 && (geo.ne || geo.nf)) {
+        cudaStream_t sd = side_stream(dev);
+        if (sd && cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming) == cudaSuccess &&
+            cudaEventCreateWithFlags(&ev_params, cudaEventDisableTiming) == cudaSuccess &&
+            cudaEventCreateWithFlags(&ev_sorted, cudaEventDisableTiming) == cudaSuccess &&
+            cudaEventCreateWithFlags(&ev_gather, cudaEventDisableTiming) == cudaSuccess &&
+            cudaEventRecord(ev_fork, st) == cudaSuccess && cudaStreamWaitEvent(sd, ev_fork, 0) == cudaSuccess) {
+            ps = sd;
+        }
+        cudaGetLastError();
+    }
+
     // incidence counts and weight parameters
     if (geo.ne) {
         ++nl;
-        k_count_slots<<<std::min(nblk(2 * (int64_t)geo.ne, T), 4096), T, 0, st>>>(geo.E, 2 * (int64_t)geo.ne, geo.nev, ecnt);
+        k_count_slots<<<std::min(nblk(2 * (int64_t)geo.ne, T), 4096), T, 0, ps>>>(geo.E, 2 * (int64_t)geo.ne, geo.nev, ecnt);
         ++nl;
-        k_edge_params<<<nblk(geo.ne, T), T, 0, st>>>(geo.E, geo.ne, geo.nev, ecnt, t->params, geo.np, bs);
+        k_edge_params<<<nblk(geo.ne, T), T, 0, ps>>>(geo.E, geo.ne, geo.nev, ecnt, t->params, geo.np, bs);
     }
     if (geo.nf) {
         ++nl;
-        k_count_slots<<<std::min(nblk(3 * (int64_t)geo.nf, T), 4096), T, 0, st>>>(geo.F, 3 * (int64_t)geo.nf, geo.ntv, vcnt);
+        k_count_slots<<<std::min(nblk(3 * (int64_t)geo.nf, T), 4096), T, 0, ps>>>(geo.F, 3 * (int64_t)geo.nf, geo.ntv, vcnt);
         ++nl;
-        k_edge_insert<<<nblk(3 * (int64_t)geo.nf, T), T, 0, st>>>(geo.F, geo.nf, hkeys, hcnt, hcap - 1);
+        k_edge_insert<<<nblk(3 * (int64_t)geo.nf, T), T, 0, ps>>>(geo.F, geo.nf, hkeys, hcnt, hcap - 1);
         ++nl;
-        k_tri_params<<<nblk(geo.nf, T), T, 0, st>>>(geo.F, geo.nf, geo.ntv, vcnt, hkeys, hcnt, hcap - 1, t->params,
+        k_tri_params<<<nblk(geo.nf, T), T, 0, ps>>>(geo.F, geo.nf, geo.ntv, vcnt, hkeys, hcnt, hcap - 1, t->params,
                                                      geo.np + geo.ne, bs);
     }
+    if (ps != st) cudaEventRecord(ev_params, ps);
     if (n > 0) {
         // Morton order
         ++nl;
@@ -721,6 +762,14 @@ extern "C" int sd_build(const sd_geometry* g, float alpha, float beta, const sd_
                                                                  ST_TIMEOUT, st, &nl);
         unsigned long long* sk = where ? k1 : k0;
         int* sv = where ? v1 : v0;
+        // the gather needs the sorted order and the parameters
+        if (ps != st) {
+            cudaEventRecord(ev_sorted, st);
+            cudaStreamWaitEvent(ps, ev_sorted, 0);
+        }
+        ++nl;
+        k_gather<<<nblk(n, T), T, 0, ps>>>(geo, sv, t->params, t->hdr, t->ext, t->sorted);
+        if (ps != st) cudaEventRecord(ev_gather, ps);
         // topology
         if (nb > 1) {
             ++nl;
@@ -728,14 +777,16 @@ extern "C" int sd_build(const sd_geometry* g, float alpha, float beta, const sd_
         }
         ++nl;
         k_super_root<<<1, 1, 0, st>>>(t->nodes, t->nw2, nb);
-        // aggregates
+        // aggregates (far-field weights use A)
+        if (ps != st) cudaStreamWaitEvent(st, ev_params, 0);
         ++nl;
         k_aggregate<<<nblk(nb, T), T, 0, st>>>(geo, sv, L, nb, t->left, pint, pleaf, t->node_box, t->node_count,
                                                 npts, t->leaf_box, t->leaf_count, lpts, visits, t->nodes, t->nw2,
                                                 bs, S, t->weights_unit);
-        ++nl;
-        k_gather<<<nblk(n, T), T, 0, st>>>(geo, sv, t->params, t->hdr, t->ext, t->sorted);
+        if (ps != st) cudaStreamWaitEvent(st, ev_gather, 0);
     }
+    for (cudaEvent_t e : {ev_fork, ev_params, ev_sorted, ev_gather})
+        if (e) cudaEventDestroy(e);
     ++nl;
     k_finalize<<<1, 32, 0, st>>>(bs, t->weights_unit, t->sc, t->status);
     cudaFreeAsync(tmp, st);
