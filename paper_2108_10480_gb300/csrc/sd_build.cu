@@ -338,10 +338,10 @@ __device__ __forceinline__ void write_slot(SdNode* nodes, float2* nw2, int rec, 
 // holds only points, then climbs; the second child to arrive at a node
 // merges both children and continues (no thread ever waits).
 __global__ void k_aggregate(Geo g, const int* __restrict__ sorted, int L, int nb, const int* __restrict__ left,
-                            const int* __restrict__ parent_int, const int* __restrict__ parent_leaf,
-                            float* node_box, int* node_count, int* node_pts, float* leaf_box, int* leaf_count,
-                            int* leaf_pts, int* visits, SdNode* nodes, float2* nw2, const BuildScalars* bs, float S,
-                            int unit)
+                            const int* __restrict__ right, const int* __restrict__ parent_int,
+                            const int* __restrict__ parent_leaf, float* node_box, int* node_count, int* node_pts,
+                            float* leaf_box, int* leaf_count, int* leaf_pts, int* visits, SdNode* nodes,
+                            float2* nw2, const BuildScalars* bs, float S, int unit)
 {
     int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= nb) return;
@@ -370,42 +370,46 @@ __global__ void k_aggregate(Geo g, const int* __restrict__ sorted, int L, int nb
     float nw = pts ? (float)count : __fmul_rn((float)count, wfar);
     int par = nb > 1 ? parent_leaf[b] : -1;
     if (par < 0) { write_slot(nodes, nw2, nb - 1, 0, lo, hi, nw); return; }
-    write_slot(nodes, nw2, par, left[par] == -(b + 1) ? 0 : 1, lo, hi, nw);
+    int from = -(b + 1);        // the child this thread arrives from
+    int lr = __ldg(&left[par]), rr = __ldg(&right[par]);
+    write_slot(nodes, nw2, par, lr == from ? 0 : 1, lo, hi, nw);
     int node = par;
+    // Up the tree: the second thread to reach a node merges its own child's
+    // aggregates (still in registers) with the sibling's, which the first
+    // thread published before its increment. The topology arrays are
+    // read-only here, so the next level's references are fetched early.
     while (node >= 0) {
+        const int pp = __ldg(&parent_int[node]);
+        const int plr = pp >= 0 ? __ldg(&left[pp]) : 0, prr = pp >= 0 ? __ldg(&right[pp]) : 0;
         __threadfence();
         if (atomicAdd(&visits[node], 1) == 0) return;
         __threadfence();
-        // both children are final: merge them
-        const SdNode* rn = &nodes[node];
-        int refs[2] = {__ldcg(&rn->d.x), __ldcg(&rn->d.y)};
-        float nlo[3] = {INFINITY, INFINITY, INFINITY}, nhi[3] = {-INFINITY, -INFINITY, -INFINITY};
-        int ncount = 0, npts = 1;
-        for (int c = 0; c < 2; ++c) {
-            const float* bx;
-            int cc, cp;
-            if (refs[c] < 0) {
-                int lb = -refs[c] - 1;
-                bx = leaf_box + 6 * lb;
-                cc = __ldcg(&leaf_count[lb]); cp = __ldcg(&leaf_pts[lb]);
-            } else {
-                bx = node_box + 6 * refs[c];
-                cc = __ldcg(&node_count[refs[c]]); cp = __ldcg(&node_pts[refs[c]]);
-            }
-            for (int j = 0; j < 3; ++j) {
-                nlo[j] = fminf(nlo[j], __ldcg(&bx[j]));
-                nhi[j] = fmaxf(nhi[j], __ldcg(&bx[3 + j]));
-            }
-            ncount += cc;
-            npts &= cp;
+        const int sib = lr == from ? rr : lr;
+        const float* bx;
+        int cc, cp;
+        if (sib < 0) {
+            const int lb = -sib - 1;
+            bx = leaf_box + 6 * lb;
+            cc = __ldcg(&leaf_count[lb]); cp = __ldcg(&leaf_pts[lb]);
+        } else {
+            bx = node_box + 6 * sib;
+            cc = __ldcg(&node_count[sib]); cp = __ldcg(&node_pts[sib]);
         }
-        for (int j = 0; j < 3; ++j) { node_box[6 * node + j] = nlo[j]; node_box[6 * node + 3 + j] = nhi[j]; }
-        node_count[node] = ncount;
-        node_pts[node] = npts;
-        float nnw = npts ? (float)ncount : __fmul_rn((float)ncount, wfar);
-        int pp = parent_int[node];
-        if (pp < 0) { write_slot(nodes, nw2, nb - 1, 0, nlo, nhi, nnw); return; }
-        write_slot(nodes, nw2, pp, left[pp] == node ? 0 : 1, nlo, nhi, nnw);
+        for (int j = 0; j < 3; ++j) {
+            lo[j] = fminf(lo[j], __ldcg(&bx[j]));
+            hi[j] = fmaxf(hi[j], __ldcg(&bx[3 + j]));
+        }
+        count += cc;
+        pts &= cp;
+        for (int j = 0; j < 3; ++j) { node_box[6 * node + j] = lo[j]; node_box[6 * node + 3 + j] = hi[j]; }
+        node_count[node] = count;
+        node_pts[node] = pts;
+        const float nnw = pts ? (float)count : __fmul_rn((float)count, wfar);
+        if (pp < 0) { write_slot(nodes, nw2, nb - 1, 0, lo, hi, nnw); return; }
+        write_slot(nodes, nw2, pp, plr == node ? 0 : 1, lo, hi, nnw);
+        from = node;
+        lr = plr;
+        rr = prr;
         node = pp;
     }
 }
@@ -780,7 +784,8 @@ extern "C" int sd_build(const sd_geometry* g, float alpha, float beta, const sd_
         // aggregates (far-field weights use A)
         if (ps != st) cudaStreamWaitEvent(st, ev_params, 0);
         ++nl;
-        k_aggregate<<<nblk(nb, T), T, 0, st>>>(geo, sv, L, nb, t->left, pint, pleaf, t->node_box, t->node_count,
+        k_aggregate<<<nblk(nb, T), T, 0, st>>>(geo, sv, L, nb, t->left, t->right, pint, pleaf, t->node_box,
+                                                t->node_count,
                                                 npts, t->leaf_box, t->leaf_count, lpts, visits, t->nodes, t->nw2,
                                                 bs, S, t->weights_unit);
         if (ps != st) cudaStreamWaitEvent(st, ev_gather, 0);
