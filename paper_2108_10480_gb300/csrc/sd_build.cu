@@ -501,7 +501,9 @@ size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // One library-owned non-blocking stream per device for the build's
 // independent branch (weight parameters and the leaf-order gather run there
-// beside the Morton sort, the topology and the aggregates).
+// beside the Morton sort, the topology and the aggregates). Every build on
+// the device shares it, so concurrent builds queue their branches behind
+// one another; each build's own stream waits only for its own events.
 static std::mutex g_side_mu;
 static cudaStream_t g_side[64] = {};
 
