@@ -1,0 +1,58 @@
+"""Host-side pieces of bench.py that need no GPU: the nvidia-smi clock
+samples are kept only inside the timed window (by their timestamps), and
+throttle reasons seen there are reported."""
+import time
+
+import bench
+
+
+def _line(t, mhz, power_cap=False):
+    stamp = time.strftime("%Y/%m/%d %H:%M:%S", time.localtime(t)) + ".%03d" % int(1000 * (t % 1.0))
+    cap = "Active" if power_cap else "Not Active"
+    return f"{stamp}, 0, {mhz}, 2070, 900.00, 0x0, Not Active, Not Active, Not Active, {cap}"
+
+
+class _Proc:
+    def terminate(self):
+        pass
+
+    def wait(self, timeout=None):
+        pass
+
+
+def _clocks(tmp_path, t0, lines):
+    c = bench._Clocks.__new__(bench._Clocks)
+    c.path = str(tmp_path / "clocks.csv")
+    (tmp_path / "clocks.csv").write_text("\n".join(lines) + "\n")
+    c.p = _Proc()
+    c.f = open(str(tmp_path / "unused"), "w")
+    c.t0 = t0
+    return c
+
+
+def test_timestamp_parse():
+    t = 1_800_000_000.25
+    s = time.strftime("%Y/%m/%d %H:%M:%S", time.localtime(t)) + ".250"
+    assert abs(bench._Clocks._stamp(s) - t) < 1e-6
+    assert bench._Clocks._stamp("not a time") is None
+
+
+def test_window_keeps_samples_inside(tmp_path, monkeypatch):
+    now = time.time()
+    t0 = now - 1.0
+    lines = [_line(t0 - 2.0, 1000), _line(t0 + 0.2, 2070), _line(t0 + 0.5, 2070, power_cap=True),
+             _line(t0 + 0.8, 2040), _line(now + 3.0, 500)]
+    c = _clocks(tmp_path, t0, lines)
+    monkeypatch.setattr(bench.time, "sleep", lambda s: None)
+    r = c.stop()
+    assert r["samples"] == 3 and r["sm_mhz"] == 2070.0 and r["reasons"] == ["sw_power_cap"]
+
+
+def test_short_window_takes_the_neighbouring_samples(tmp_path, monkeypatch):
+    now = time.time()
+    t0 = now - 0.01                      # shorter than the sampling interval
+    lines = [_line(t0 - 0.5, 2000), _line(now + 0.5, 2070)]
+    c = _clocks(tmp_path, t0, lines)
+    monkeypatch.setattr(bench.time, "sleep", lambda s: None)
+    r = c.stop()
+    assert r["samples"] == 2 and r["sm_mhz"] == 2035.0
