@@ -108,6 +108,21 @@ def _src_hash():
     return h.hexdigest()[:16]
 
 
+def _tensor_roofline(tflops):
+    """The surrogate network's GEMM rate against the measured dense bf16
+    peak of this machine's GPUs (burst: the kernel is timed alone), else the
+    fallback figure."""
+    peak, src = 1900.0, "fallback 1.9 PFLOP/s bf16"
+    try:
+        d = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        if float(d.get("bf16_tflops", 0)) > 0:
+            peak, src = float(d["bf16_tflops"]), "measured bf16 burst (cuBLAS)"
+    except (OSError, ValueError, TypeError):
+        pass
+    return {"bound": "tensor", "achieved": tflops, "peak": peak, "unit": "TFLOP/s", "frac": tflops / peak,
+            "peak_source": src}
+
+
 def _traffic(kernel_hash):
     """Per-launch DRAM bytes of the traversal kernel from the committed ncu
     summary, or None if the kernel changed since it was captured."""
@@ -734,7 +749,8 @@ def _surrogate_leg(args, dev, reps=3):
             "speedup": ms_bh / ms_sur, "value": n / (ms_sur / 1e3), "unit": "queries/s",
             "ms_lower_bound_all": ms_lb,
             "mlp_forward": {"queries": nr, "ms": ms_mlp, "queries_per_s": nr / (ms_mlp / 1e3),
-                            "tflops": nr * MLP_FLOPS / (ms_mlp / 1e3) / 1e12, "flops_per_query": MLP_FLOPS},
+                            "tflops": nr * MLP_FLOPS / (ms_mlp / 1e3) / 1e12, "flops_per_query": MLP_FLOPS,
+                            "roofline": _tensor_roofline(nr * MLP_FLOPS / (ms_mlp / 1e3) / 1e12)},
             "abs_err_m": {"p50": _pct(err, 0.5), "p99": _pct(err, 0.99), "max": float(err.max().item())},
             "lb_alone_abs_err_m": {"p50": _pct(err_lb, 0.5), "p99": _pct(err_lb, 0.99)},
             "grad_err": {"p50": _pct(gerr, 0.5), "p99": _pct(gerr, 0.99), "max": float(gerr.max().item())}}

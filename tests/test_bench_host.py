@@ -56,3 +56,13 @@ def test_short_window_takes_the_neighbouring_samples(tmp_path, monkeypatch):
     monkeypatch.setattr(bench.time, "sleep", lambda s: None)
     r = c.stop()
     assert r["samples"] == 2 and r["sm_mhz"] == 2035.0
+
+
+def test_tensor_roofline_fraction(tmp_path, monkeypatch):
+    r = bench._tensor_roofline(288.0)
+    assert r["bound"] == "tensor" and r["unit"] == "TFLOP/s"
+    assert abs(r["frac"] - 288.0 / r["peak"]) < 1e-12
+    # without the measured peaks the fallback figure is used and said so
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    r = bench._tensor_roofline(190.0)
+    assert r["peak"] == 1900.0 and r["peak_source"].startswith("fallback") and abs(r["frac"] - 0.1) < 1e-12
