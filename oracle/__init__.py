@@ -13,9 +13,9 @@ Layout:
   pose.py        rigid pose map, outer LSE and pose gradient (numpy, FP64)
   mlp.py         Fourier-feature MLP forward/backward (numpy, FP64)
 
-Parity unpinned: the triangle weight between its constraint points and the
-``paper_metric`` (alpha-scaled barycentric gradient) variant; everything else
-is pinned by tests/test_oracle_*.py.
+Parity unpinned: the ``paper_metric`` (alpha-scaled barycentric gradient)
+variant; everything else is pinned by tests/test_oracle_*.py (the triangle
+weight everywhere by an exact rational minimum-norm solve of App. C.3).
 """
 from __future__ import annotations
 

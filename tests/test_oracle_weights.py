@@ -132,3 +132,46 @@ def test_isolated_triangle_polynomial_goes_negative():
     phi = np.random.default_rng(1).dirichlet([1, 1, 1], 20000)[:, 1:]
     c = _poly(1.0, 1.0)
     assert _eval(c, phi[:, 0], phi[:, 1]).min() < 0
+
+
+def test_tri_min_norm_exact_rational():
+    """The triangle weight everywhere (not only at its constraint points):
+    App. C.3's constraints rebuilt from the text in exact rational arithmetic
+    (sympy, independent of the oracle's matrix), their minimum-norm solution
+    x = A^T y with A A^T y = b solved exactly, and the oracle's coefficients
+    compared with it."""
+    sp = pytest.importorskip("sympy")
+    p1, p2, t = sp.symbols("p1 p2 t")
+    keys = [(a, b) for a in range(8) for b in range(8) if a + b <= 7]
+    cs = sp.symbols("c0:%d" % len(keys))
+    w = sum(c * p1 ** a * p2 ** b for c, (a, b) in zip(cs, keys))
+    third = sp.Rational(1, 3)
+    eqs = []     # (linear form in cs, right-hand side column: 0 vertex, 1 edge, 2 centre, None zero)
+    for pt in [(0, 0), (1, 0), (0, 1)]:
+        eqs.append((w.subs({p1: pt[0], p2: pt[1]}), 0))
+    for pt in [(third, 0), (2 * third, 0), (0, third), (0, 2 * third), (third, 2 * third), (2 * third, third)]:
+        eqs.append((w.subs({p1: pt[0], p2: pt[1]}), 1))
+    eqs.append((w.subs({p1: third, p2: third}), 2))
+    # zero derivative across each side: d/dphi1 on phi1 = 0, d/dphi2 on
+    # phi2 = 0, (d/dphi1 + d/dphi2) on phi1 + phi2 = 1 (both directions)
+    lines = [(sp.diff(w, p1), {p1: 0, p2: t}), (sp.diff(w, p2), {p1: t, p2: 0}),
+             (sp.diff(w, p1) + sp.diff(w, p2), {p1: t, p2: 1 - t}),
+             (sp.diff(w, p1) + sp.diff(w, p2), {p1: 1 - t, p2: t})]
+    for expr, sub in lines:
+        poly = sp.Poly(sp.expand(expr.subs(sub)), t)
+        for coeff in poly.all_coeffs():
+            eqs.append((coeff, None))
+    A = sp.Matrix([[sp.diff(e, c) for c in cs] for e, _ in eqs])
+    M = A * A.T
+    X = W.tri_basis()
+    idx = {m: i for i, m in enumerate(W.TRI_EXPONENTS)}
+    scale = np.abs(X).max()
+    for col in range(3):
+        b = sp.Matrix([1 if r == col else 0 for _, r in eqs])
+        sol, params = M.gauss_jordan_solve(b)
+        y = sol.subs({p: 0 for p in params})
+        x = A.T * y                                  # unique: the minimum-norm solution
+        assert (A * x - b).is_zero_matrix            # the constraints hold exactly
+        ref = np.array([float(x[i]) for i in range(len(keys))])
+        got = np.array([X[idx[k], col] for k in keys])
+        assert np.abs(got - ref).max() <= 1e-10 * scale, (col, np.abs(got - ref).max())
