@@ -1,7 +1,8 @@
 """Pins of the oracle's weight polynomials (App. C) against what the paper
 fixes: the constraint values, the zero normal derivatives, symmetry, the
-13-coefficient structure, the scale A, plus an independent QR-based
-minimum-norm solve."""
+13-coefficient structure, the scale A, an independent QR-based
+minimum-norm solve, and the exact minimum-norm solution of the triangle
+system rebuilt in rational arithmetic."""
 import numpy as np
 import pytest
 import scipy.linalg
