@@ -233,7 +233,11 @@ constexpr int KF1 = 80;                 // layer-1 K (67 features + zero padding
 constexpr int TMEM_COLS = 512;          // per group (256 columns each): accumulator [0,128),
                                         // dsilu(z1) [128,192), dsilu(z2) [192,256) (binary16 pairs)
 constexpr int SZ_W1 = HID * KF1 * 2, SZ_W = HID * HID * 2, SZ_X = TM * HID * 2;
-constexpr int O_W1 = 0, O_W2 = O_W1 + SZ_W1, O_W3 = O_W2 + SZ_W, O_X = O_W3 + SZ_W, O_F32 = O_X + 2 * SZ_X;
+// per group, the complementary sine or cosine of every Fourier feature
+// column (fp32, [64 columns][128 rows]) kept from the forward pass for dy/dx
+constexpr int SZ_FC = TM * 2 * NF * 4;
+constexpr int O_W1 = 0, O_W2 = O_W1 + SZ_W1, O_W3 = O_W2 + SZ_W, O_X = O_W3 + SZ_W, O_FC = O_X + 2 * SZ_X,
+              O_F32 = O_FC + 2 * SZ_FC;
 // fp32 area: b1, b2, b3, w4 (bf16-rounded) [4 x 128], B [96], b4, then per
 // group the second column half's partial sums: y [128], dy/dxh [128 x 3],
 // then s * w4 [128]
@@ -481,6 +485,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mlp_tc(const float* __restric
     const uint32_t bar_a = smem_addr(smem + O_BAR + 8 * g), xa = smem_addr(smem + O_X + g * SZ_X);
     const uint32_t w1a = smem_addr(smem + O_W1), w2a = smem_addr(smem + O_W2), w3a = smem_addr(smem + O_W3);
     unsigned char* X = smem + O_X + g * SZ_X;
+    float* FC = reinterpret_cast<float*>(smem + O_FC + g * SZ_FC);
     const float* w4 = F32 + F_BIAS + 3 * HID;
     const float* Bq = F32 + F_BQ;
     float* yp_h = F32 + F_YP + g * TM;          // the second half's partial y
@@ -519,6 +524,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mlp_tc(const float* __restric
                     float sv, cv;
                     sincospi_tc(pp, &sv, &cv);
                     v = c < 3 + NF ? sv : cv;
+                    FC[(c - 3) * TM + row] = c < 3 + NF ? cv : sv;   // what dy/dx needs for this column
                 }
                 f[j] = v;
             }
@@ -631,12 +637,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mlp_tc(const float* __restric
                                 gg[c] += gv;
                             } else if (c < NIN) {
                                 const int m = c < 3 + NF ? c - 3 : c - 3 - NF;
-                                const float pp =
-                                    fmaf(Bq[3 * m], xh[0], fmaf(Bq[3 * m + 1], xh[1], Bq[3 * m + 2] * xh[2]));
-                                float sv, cv;
-                                sincospi_tc(pp, &sv, &cv);
-                                const float k = c < 3 + NF ? gv * 3.14159265358979f * cv
-                                                           : -gv * 3.14159265358979f * sv;
+                                const float o = FC[(c - 3) * TM + row];   // cos for a sine column, sin for a cosine one
+                                const float k = c < 3 + NF ? gv * 3.14159265358979f * o
+                                                           : -gv * 3.14159265358979f * o;
                                 gg[0] = fmaf(k, Bq[3 * m], gg[0]);
                                 gg[1] = fmaf(k, Bq[3 * m + 1], gg[1]);
                                 gg[2] = fmaf(k, Bq[3 * m + 2], gg[2]);
