@@ -225,7 +225,7 @@ void sd_batch_free(sd_batch* b);
  * frame = host float[7] = (c_x, c_y, c_z, h_x, h_y, h_z, s): box centre,
  * half extents (> 0) and output scale; SD_ERR_INVALID_ARG otherwise.
  *   sd_mlp_forward: device x [n,3] -> y [n] and, if dydx is not NULL,
- *     dy/dx [n,3] (tcgen05 tensor-core kernel, one CTA with 158 KB of shared
+ *     dy/dx [n,3] (tcgen05 tensor-core kernel, one CTA with 219 KB of shared
  *     memory and all 512 tensor-memory columns per SM; features, a1, a2 and
  *     the back-propagated factors rounded to bfloat16, dsilu(z1), dsilu(z2)
  *     to binary16; input gradient by back-propagation). A tile whose
