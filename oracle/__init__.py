@@ -13,9 +13,10 @@ Layout:
   pose.py        rigid pose map, outer LSE and pose gradient (numpy, FP64)
   mlp.py         Fourier-feature MLP forward/backward (numpy, FP64)
 
-Parity unpinned: the ``paper_metric`` (alpha-scaled barycentric gradient)
-variant; everything else is pinned by tests/test_oracle_*.py (the triangle
-weight everywhere by an exact rational minimum-norm solve of App. C.3).
+Every function is pinned by tests/test_oracle_*.py: the triangle weight
+everywhere by an exact rational minimum-norm solve of App. C.3, the
+``paper_metric`` (alpha-scaled barycentric gradient) variant by its defining
+relation to the exact gradient.
 """
 from __future__ import annotations
 

@@ -158,3 +158,34 @@ def test_empty_scene_is_infinite():
     s = oracle.Scene()
     v, g, dm = s.brute(np.zeros((2, 3)), 10.0)
     assert np.all(np.isinf(v)) and np.all(g == 0)
+
+
+def test_paper_metric_rescales_only_the_weight_term():
+    """The paper_metric variant (reading R4: the barycentric gradients taken
+    in the alpha-scaled metric) divides the weight-gradient part of each
+    term's vector by alpha once more and changes nothing else: per primitive
+    vec_pm = grad d + (vec - grad d) / alpha, the value is unchanged, and the
+    LogSumExp gradient is the softmax mix of those vectors."""
+    V, F = synth.icosphere(2)
+    V = synth.perturb_radial(V, 0.02, 3)
+    sc = oracle.Scene(tri_V=V, tri_F=F)
+    q = synth.shell_queries(40, frac_shell=1.0, r_lo=0.95, r_hi=1.05, seed=8)
+    alpha = 20.0
+    v0, g0, _ = sc.brute(q, alpha)
+    v1, g1, _ = sc.brute(q, alpha, paper_metric=True)
+    assert np.array_equal(v0, v1)
+    for k in range(len(q)):
+        ts, vs = [], []
+        for i in range(len(F)):
+            e = sc.prim_eval(i, q[k], alpha)
+            p = sc.prim_eval(i, q[k], alpha, paper_metric=True)
+            assert p["t"] == e["t"]
+            np.testing.assert_allclose(p["vec"], e["grad_d"] + (e["vec"] - e["grad_d"]) / alpha, rtol=0, atol=1e-12)
+            ts.append(e["t"])
+            vs.append(p["vec"])
+        ts = np.array(ts)
+        s = np.exp(ts - ts.max())
+        ref = (s[:, None] * np.array(vs)).sum(0) / s.sum()
+        np.testing.assert_allclose(g1[k], ref, rtol=1e-10, atol=1e-12)
+    # and it differs from the exact gradient where the weights vary
+    assert np.abs(g1 - g0).max() > 1e-6
