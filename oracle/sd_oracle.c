@@ -713,7 +713,7 @@ double orc_simplex_closest(const double *A, int na, const double *B, int nb, dou
     double best = INFINITY;
     for (int sa = 1; sa < (1 << na); ++sa)
         for (int sb = 1; sb < (1 << nb); ++sb) {
-            int ia[3], ib[3], ka = 0, kb = 0;
+            int ia[3] = {0, 0, 0}, ib[3] = {0, 0, 0}, ka = 0, kb = 0;
             for (int i = 0; i < na; ++i) if ((sa >> i) & 1) ia[ka++] = i;
             for (int j = 0; j < nb; ++j) if ((sb >> j) & 1) ib[kb++] = j;
             const double *a0 = A + 3 * ia[0], *b0 = B + 3 * ib[0];
