@@ -11,6 +11,15 @@ fused value + gradient) over one batch resident in HBM. The L2 is flushed
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
+Roofline: the traversal is bound by the FP32 pipe with the MUFU pipe as a
+co-bound (its HBM traffic is a few MB per launch). Its work per launch is
+the method's per-unit cost (METHOD_FLOPS, METHOD_MUFU) times the kernel's
+work counts (Barnes-Hut tests, far-field accepts, exact leaf terms); the
+peaks are measured on the GPU by the library's own FMA and ex2 probes,
+scaled to the clock sampled during the timed region. The same figures are
+reported for the nine (alpha, beta) cells of the icosphere workload and for
+the street point queries (`cells`).
+
 N > 1 runs under torchrun, one rank per GPU: every rank builds the same tree
 and evaluates its own 262,144 queries (weak scaling, no data-path
 collective); the time is the max over ranks.
@@ -24,6 +33,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -39,22 +49,26 @@ UNIT = "queries/s"
 ALPHA, BETA, LEAF = 200.0, 0.5, 1
 M_QUERIES = 262144
 
-# FP32 operations per unit of Barnes-Hut work in the traversal kernel, hand
-# counted from its source (add/sub/mul/min/max = 1, FMA = 2; MUFU ops and
-# comparisons/selects not counted): one Barnes-Hut test of a child box, the
-# extra work of an accepted far-field node, and one exact triangle term
-# (closest point, degree-7 weight by de Casteljau and its gradient, LSE
-# update).
-FLOPS_TEST = 26
-FLOPS_FAR = 26
-FLOPS_TRI = 737
-# FP32 peak: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz maximum SM clock
-SMS, LANES, SM_MAX_GHZ = 152, 128, 2.07
+# Work of the method per unit, a hand count of the method's own arithmetic
+# (not of any kernel): FP32 flops (add/sub/mul/min/max 1, FMA 2) and MUFU
+# operations (exponential, (reciprocal) square root, reciprocal).
+#   test   one Barnes-Hut test: point-to-AABB squared distance, one compare
+#   far    an accepted far field: its distance, weight, exponential, LSE update
+#   point / seg / tri   one exact leaf term: closest point, weight and its
+#          gradient, LSE update
+METHOD_FLOPS = {"test": 20, "far": 12, "point": 14, "seg": 45, "tri": 160}
+METHOD_MUFU = {"test": 0, "far": 3, "point": 2, "seg": 3, "tri": 3}
+# The traversal kernel's own hand count of the same units (its source:
+# packed two-child test, branch-free far field, de Casteljau weight),
+# reported beside the method's figure only.
+KERNEL_FLOPS = {"test": 26, "far": 26, "tri": 737}
 # tensor-core flops per query of the surrogate network, value and input
 # gradient: forward 80x128 + 2 x 128x128 MACs (layer 1 padded to 80 inputs),
 # backward 2 x 128x128 + 128x80 MACs, 2 flops per MAC
 MLP_FLOPS = 2 * 2 * (80 * 128 + 2 * 128 * 128)
-FP32_PEAK_TFLOPS = SMS * LANES * 2 * SM_MAX_GHZ / 1e3
+# the nine (alpha, beta) cells of the icosphere workload
+CELL_ALPHAS = (50.0, 200.0, 1000.0)
+CELL_BETAS = (0.25, 0.5, 1.0)
 
 
 _SCENE = {}
@@ -81,7 +95,8 @@ def _args_from(argv):
     p.add_argument("--beta", type=float, default=BETA)
     p.add_argument("--leaf-size", type=int, default=LEAF)
     p.add_argument("--queries", type=int, default=M_QUERIES)
-    p.add_argument("--no-extras", action="store_true", help="skip plain/e2e/cpu baseline legs")
+    p.add_argument("--no-extras", action="store_true", help="skip plain/e2e/cpu baseline and application legs")
+    p.add_argument("--no-cells", action="store_true", help="skip the per-(alpha, beta) cell table")
     return p.parse_args(argv)
 
 
@@ -136,23 +151,118 @@ def _traffic(kernel_hash):
     return d.get("dram_bytes_per_launch")
 
 
+def _pipe_peaks(dev, clocks=None, target_ms=25.0):
+    """FP32 and MUFU pipe rates measured on this GPU with the library's own
+    probes (sd_peak_probe): fma.rn.f32 chains, fma.rn.f32x2 chains and
+    ex2.approx chains on a full-occupancy grid (8 blocks of 256 threads per
+    SM), each launch sized to about target_ms and timed with CUDA events
+    (median of 5 after one warm-up). The FP32 peak is the better of the two
+    FMA forms (an FMA is 2 flops); the MUFU peak is the ex2 rate."""
+    import ctypes
+
+    import torch
+
+    from paper_2108_10480_gb300 import _native, lib
+    L = lib()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    blocks = sms * 8
+    sink = torch.empty(blocks * 256, device=dev)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ops = ctypes.c_double()
+    rates = {}
+
+    def launch(kind, iters):
+        _native.check(L.sd_peak_probe(kind, blocks, iters, ctypes.c_void_p(sink.data_ptr()), ctypes.byref(ops),
+                                      ctypes.c_void_p(stream.cuda_stream)), "sd_peak_probe")
+
+    if clocks:
+        clocks.begin("pipe_probes")
+    for kind, name in ((0, "ffma"), (1, "ffma2"), (2, "ex2")):
+        iters = 64
+        launch(kind, iters)
+        e0.record(stream)
+        launch(kind, iters)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        iters = max(64, int(iters * target_ms / max(e0.elapsed_time(e1), 1e-3)))
+        launch(kind, iters)
+        ts = []
+        for _ in range(5):
+            e0.record(stream)
+            launch(kind, iters)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        rates[name] = {"ops_per_s": ops.value / (statistics.median(ts) / 1e3), "ms": statistics.median(ts),
+                       "iters": iters}
+    if clocks:
+        clocks.end("pipe_probes")
+    fp32 = 2.0 * max(rates["ffma"]["ops_per_s"], rates["ffma2"]["ops_per_s"]) / 1e12
+    return {"fp32_tflops": fp32, "mufu_gops": rates["ex2"]["ops_per_s"] / 1e9, "sms": sms, "blocks": blocks,
+            "probes": {k: dict(v, ops_per_s=v["ops_per_s"]) for k, v in rates.items()},
+            "source": "measured: sd_peak_probe fma.rn.f32 / fma.rn.f32x2 / ex2.approx.ftz.f32 chains, "
+                      f"{blocks} x 256 threads, CUDA events, median of 5"}
+
+
+def _scale_peaks(peaks, mhz_probe, mhz_run):
+    """The measured peaks at the clock the timed kernel ran at: the probes'
+    rates scaled by (median SM clock in the timed region) / (median SM clock
+    during the probes). Unchanged when either clock is unknown."""
+    if not mhz_probe or not mhz_run:
+        return dict(peaks, clock_scale=1.0)
+    k = float(mhz_run) / float(mhz_probe)
+    return dict(peaks, fp32_tflops=peaks["fp32_tflops"] * k, mufu_gops=peaks["mufu_gops"] * k, clock_scale=k)
+
+
+def _alu_roofline(work, ms, peaks, leaf_kind="tri"):
+    """Roofline of one traversal launch against the FP32 pipe with the MUFU
+    pipe as co-bound: work = per-launch totals of Barnes-Hut tests, far-field
+    accepts and exact leaf terms (the kernel's work counts, identical to the
+    oracle's); each unit is charged the method's own per-unit cost
+    (METHOD_FLOPS / METHOD_MUFU, leaf terms at `leaf_kind`'s cost); ms = the
+    launch's duration. frac is the larger of the two pipes' fractions, and
+    achieved / peak / unit are that pipe's."""
+    t = ms / 1e3
+    flops = (work["test"] * METHOD_FLOPS["test"] + work["far"] * METHOD_FLOPS["far"]
+             + work["leaf"] * METHOD_FLOPS[leaf_kind])
+    mufu = work["far"] * METHOD_MUFU["far"] + work["leaf"] * METHOD_MUFU[leaf_kind]
+    fp32 = flops / t / 1e12
+    mu = mufu / t / 1e9
+    f_fp32, f_mufu = fp32 / peaks["fp32_tflops"], mu / peaks["mufu_gops"]
+    fp32_line = {"pipe": "fp32", "achieved": fp32, "peak": peaks["fp32_tflops"], "unit": "TFLOP/s", "frac": f_fp32}
+    mufu_line = {"pipe": "mufu", "achieved": mu, "peak": peaks["mufu_gops"], "unit": "Gop/s", "frac": f_mufu}
+    bind, co = (fp32_line, mufu_line) if f_fp32 >= f_mufu else (mufu_line, fp32_line)
+    return {"bound": "alu", "achieved": bind["achieved"], "peak": bind["peak"], "unit": bind["unit"],
+            "frac": bind["frac"], "binding_pipe": bind["pipe"], "co_bound": co,
+            "work_per_launch": {"flops": flops, "mufu_ops": mufu, "tests": work["test"], "far_accepts": work["far"],
+                                "leaf_terms": work["leaf"], "leaf_kind": leaf_kind},
+            "method_costs": {"flops": {k: METHOD_FLOPS[k] for k in ("test", "far", leaf_kind)},
+                             "mufu": {k: METHOD_MUFU[k] for k in ("test", "far", leaf_kind)}}}
+
+
 class _Clocks:
-    """nvidia-smi sampling of SM clocks and throttle reasons every 50 ms.
-    Started before the warm-up (nvidia-smi takes a moment to begin); only
-    the samples stamped inside the timed window [mark(), stop()] are kept,
-    widened to the nearest sample on each side when the window is shorter
-    than the sampling interval."""
+    """nvidia-smi sampling of SM clocks and throttle reasons every 50 ms into
+    a temporary file. Started before the warm-up (nvidia-smi takes a moment
+    to begin); only the samples stamped inside the timed window [mark(),
+    stop()] are kept, widened to the nearest sample on each side when the
+    window is shorter than the sampling interval. Further named windows
+    (begin(name) / end(name), e.g. the pipe probes) are summarised the same
+    way in `windows` once stop() has run."""
 
     FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    REASONS = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
 
     def __init__(self, index):
         self.p = None
         self.t0 = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        self.spans = {}
+        self.windows = {}
+        fd, self.path = tempfile.mkstemp(prefix="sd_clocks_", suffix=".csv")
+        os.close(fd)
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
             self.p = subprocess.Popen(
                 ["nvidia-smi", "-i", str(index), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
@@ -167,6 +277,13 @@ class _Clocks:
     def mark(self):
         self.t0 = time.time()
 
+    def begin(self, name):
+        self.spans[name] = [time.time(), None]
+
+    def end(self, name):
+        if name in self.spans:
+            self.spans[name][1] = time.time()
+
     @staticmethod
     def _stamp(txt):
         """nvidia-smi's local-time stamp "YYYY/MM/DD hh:mm:ss.fff" in epoch seconds."""
@@ -175,6 +292,17 @@ class _Clocks:
             return time.mktime(time.strptime(main, "%Y/%m/%d %H:%M:%S")) + (float("0." + frac) if frac else 0.0)
         except ValueError:
             return None
+
+    @classmethod
+    def _summary(cls, rows, t0, t1):
+        inside = [r for r in rows if r[0] is not None and t0 <= r[0] <= t1]
+        if not inside:
+            before = [r for r in rows if r[0] is not None and r[0] < t0]
+            after = [r for r in rows if r[0] is not None and r[0] > t1]
+            inside = before[-1:] + after[:1] or rows[-1:]
+        reasons = sorted({nm for r in inside for nm, on in zip(cls.REASONS, r[3]) if on})
+        return {"sm_mhz": statistics.median(r[1] for r in inside), "sm_max_mhz": max(r[2] for r in inside),
+                "samples": len(inside), "interval_ms": 50, "reasons": reasons}
 
     def stop(self):
         if self.p is None:
@@ -197,18 +325,15 @@ class _Clocks:
                 rows.append((ts, float(parts[2]), float(parts[3]), [v.lower() == "active" for v in parts[6:10]]))
             except ValueError:
                 continue
+        try:
+            os.unlink(self.path)
+        except OSError:
+            pass
         if not rows:
             return None
-        t0 = self.t0 if self.t0 is not None else t1
-        inside = [r for r in rows if r[0] is not None and t0 <= r[0] <= t1]
-        if not inside:
-            before = [r for r in rows if r[0] is not None and r[0] < t0]
-            after = [r for r in rows if r[0] is not None and r[0] > t1]
-            inside = before[-1:] + after[:1] or rows[-1:]
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({nm for r in inside for nm, on in zip(names, r[3]) if on})
-        return {"sm_mhz": statistics.median(r[1] for r in inside), "sm_max_mhz": max(r[2] for r in inside),
-                "samples": len(inside), "interval_ms": 50, "reasons": reasons}
+        for name, (a, b) in self.spans.items():
+            self.windows[name] = self._summary(rows, a, b if b is not None else t1)
+        return self._summary(rows, self.t0 if self.t0 is not None else t1, t1)
 
 
 def _max_over_ranks(ms, device):
@@ -282,6 +407,7 @@ def run_ours(args):
         torch.cuda.synchronize()
 
     clocks = _Clocks(local) if rank == 0 else None
+    peaks = _pipe_peaks(dev, clocks) if rank == 0 else None
     for _ in range(max(args.warmup, 0)):
         step()
     # work counts of this workload (decisions are deterministic)
@@ -314,9 +440,20 @@ def run_ours(args):
     out = None
     if rank == 0:
         trav = statistics.mean(trav_ms)
-        flops = tot[0] * FLOPS_TEST + tot[1] * FLOPS_FAR + tot[2] * FLOPS_TRI
-        achieved = flops / (trav / 1e3) / 1e12
         kh = _src_hash()
+        pw = clocks.windows.get("pipe_probes") if clocks else None
+        pk = _scale_peaks(peaks, pw and pw["sm_mhz"], clk and clk["sm_mhz"])
+        roof = _alu_roofline({"test": tot[0], "far": tot[1], "leaf": tot[2]}, trav, pk, "tri")
+        kflops = tot[0] * KERNEL_FLOPS["test"] + tot[1] * KERNEL_FLOPS["far"] + tot[2] * KERNEL_FLOPS["tri"]
+        roof.update({"traffic": _traffic(kh), "kernel": "k_traverse<tris,grad>", "kernel_src_hash": kh,
+                     "launch_ms": trav,
+                     "peak_source": pk["source"] + f"; scaled to the timed region's clock (x{pk['clock_scale']:.4f})",
+                     "peaks": {"fp32_tflops": pk["fp32_tflops"], "mufu_gops": pk["mufu_gops"],
+                               "probes": peaks["probes"], "probe_clocks": pw},
+                     "kernel_count": {"flops_per_launch": kflops, "tflops": kflops / (trav / 1e3) / 1e12,
+                                      "frac": kflops / (trav / 1e3) / 1e12 / pk["fp32_tflops"],
+                                      "costs": dict(KERNEL_FLOPS),
+                                      "what": "the kernel's own hand count of its source (context only)"}})
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -325,21 +462,98 @@ def run_ours(args):
             "breakdown_ms": {"build_and_order": statistics.mean(build_ms), "traverse": trav},
             "work": {"bh_tests": tot[0], "far_accepts": tot[1], "leaf_triangles": tot[2],
                      "per_query": [x / M for x in tot]},
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": achieved / FP32_PEAK_TFLOPS, "traffic": _traffic(kh),
-                         "kernel": "k_traverse<tris,grad>", "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
-                         "kernel_src_hash": kh},
+            "roofline": roof,
             "gpu_launches": launches,
             "wall_s_timed": t_wall,
         }
         if clk:
             out["clocks"] = clk
+        if not args.no_cells:
+            out["cells"] = _cells(args, dev, V, F, q, pk)
         if not args.no_extras:
             out.update(_extras(args, c, V, F, q, dev, M))
+    if not args.no_extras:
+        # every rank: one body's vertices split across the ranks
+        sh = _sharded_pose_leg(dev, rank, world)
+        if out is not None:
+            out["pose_sharded"] = sh
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
     return out
+
+
+def _timed_queries(sd, q, order, val, grad, reps, flush):
+    """Median CUDA-event time of one sd_query launch over `reps` launches,
+    the L2 flushed (256 MiB write) before each, outside the timed region."""
+    import torch
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sd.query(q, out=(val, grad), order=order)
+    ts = []
+    for k in range(reps):
+        flush.fill_(k & 255)
+        e0.record(stream)
+        sd.query(q, out=(val, grad), order=order)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return statistics.median(ts)
+
+
+def _cell_row(sd, q, order, val, grad, flush, peaks, leaf_kind, reps):
+    import torch
+    M = q.shape[0]
+    _, _, cnt = sd.query(q, counts=True, order=order)
+    tot = cnt.to(torch.int64).sum(0).tolist()
+    ms = _timed_queries(sd, q, order, val, grad, reps, flush)
+    roof = _alu_roofline({"test": tot[0], "far": tot[1], "leaf": tot[2]}, ms, peaks, leaf_kind)
+    return {"queries": M, "ms": ms, "queries_per_s": M / (ms / 1e3),
+            "per_query": {"bh_tests": tot[0] / M, "far_accepts": tot[1] / M, "leaf_terms": tot[2] / M},
+            "frac": roof["frac"], "binding_pipe": roof["binding_pipe"],
+            "fp32_tflops": roof["achieved"] if roof["binding_pipe"] == "fp32" else roof["co_bound"]["achieved"],
+            "mufu_frac": roof["frac"] if roof["binding_pipe"] == "mufu" else roof["co_bound"]["frac"]}
+
+
+def _cells(args, dev, V, F, q, peaks, reps=5):
+    """The traversal (sd_query, value + gradient, Hilbert order computed
+    once outside the timing) on every (alpha, beta) cell of the icosphere
+    workload (81,920 triangles, 262,144 queries) and on the street point
+    queries (the 100,002 vertices of the posed body against 2,000,000 lidar
+    points + 50,000 wire segments, alpha 50, beta 0.5): queries/s, the work
+    counts per query and the roofline fraction with the method's per-unit
+    costs. On the street every leaf term is charged a point's cost (the
+    counts do not split points from wire segments; segments cost more, so
+    this under-counts the work)."""
+    import torch
+
+    from paper_2108_10480_gb300 import SmoothDistance
+    from paper_2108_10480_gb300 import pose as gp
+    M = q.shape[0]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    val, grad = torch.empty(M, device=dev), torch.empty(M, 3, device=dev)
+    rows = []
+    for beta in CELL_BETAS:
+        for alpha in CELL_ALPHAS:
+            sd = SmoothDistance(tris=(V, F), alpha=alpha, beta=beta, leaf_size=args.leaf_size, device=dev)
+            order = sd.query_order(q)
+            r = _cell_row(sd, q, order, val, grad, flush, peaks, "tri", reps)
+            rows.append(dict({"workload": "icosphere-L6", "alpha": alpha, "beta": beta}, **r))
+            del sd
+    s = _street()
+    b = synth.config3_body()
+    sd = SmoothDistance(points=s["points"], edges=(s["wire_V"], s["wire_E"]), alpha=50.0, beta=0.5, device=dev)
+    X0 = torch.from_numpy(b["V0"]).to(dev)
+    X, _, _ = gp.pose_query(sd, X0, np.concatenate([b["theta"], b["p"]]))
+    X = X.contiguous()
+    vs, gs = torch.empty(X.shape[0], device=dev), torch.empty(X.shape[0], 3, device=dev)
+    order = sd.query_order(X)
+    r = _cell_row(sd, X, order, vs, gs, flush, peaks, "point", reps)
+    rows.append(dict({"workload": "street 2M points + 50k wires, 100,002 body vertices", "alpha": 50.0,
+                      "beta": 0.5}, **r))
+    return {"what": "sd_query (value + gradient) per cell, median of 5 launches with the L2 flushed before each; "
+                    "frac = method work (per-unit costs of the roofline) / launch time / measured pipe peak",
+            "rows": rows}
 
 
 def _extras(args, c, V, F, q, dev, M):
@@ -867,11 +1081,59 @@ def _pose_leg(args, dev, iters=20):
             "D": float(out[0].item())}
 
 
-def _cpu_baseline(c, args, sample=None, min_seconds=0.0):
+def _sharded_pose_leg(dev, rank, world, iters=20):
+    """One body split across the ranks (strong scaling of a single
+    constraint): the 100,002-vertex body against the street (2,000,000
+    points + 50,000 wires, alpha 50, beta 0.5, alpha_q 100); each rank places
+    and queries its contiguous slice of the vertices, forms its shard's
+    partial (sd_pose_partial), and the partials are all-gathered (9 floats
+    per rank, the only exchange) and merged on the host (sd_pose_merge). The
+    result is compared with sd_pose_reduce over the whole body on this
+    rank."""
+    import torch
+
+    from paper_2108_10480_gb300 import SmoothDistance
+    from paper_2108_10480_gb300 import pose as gp
+    s = _street()
+    b = synth.config3_body()
+    pose = np.concatenate([b["theta"], b["p"]])
+    sd = SmoothDistance(points=s["points"], edges=(s["wire_V"], s["wire_E"]), alpha=50.0, beta=0.5, device=dev)
+    X0 = torch.from_numpy(b["V0"]).to(dev)
+    M = X0.shape[0]
+    a, e = rank * M // world, (rank + 1) * M // world
+    mine = X0[a:e].contiguous()
+
+    def one():
+        _, v, g = gp.pose_query(sd, mine, pose)
+        part = gp.pose_partial(mine, v, g, pose, alpha_q=100.0)
+        return gp.reduce_shards(part, pose, alpha_q=100.0)
+    for _ in range(3):
+        r = one()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(iters):
+        r = one()
+    ms = 1e3 * (time.perf_counter() - t0) / iters
+    ms = _max_over_ranks(ms, dev)
+    _, v, g = gp.pose_query(sd, X0, pose)
+    whole, _ = gp.pose_reduce(X0, v, g, pose, alpha_q=100.0)
+    whole = whole.cpu().numpy().astype(np.float64)
+    return {"what": "100,002-vertex body split over the ranks: per-rank placement + BH query + shard partial, "
+                    "9-float all-gather, host merge (host wall clock per evaluation, max over ranks)",
+            "ranks": world, "vertices_per_rank": e - a, "ms_per_evaluation": ms,
+            "value": M / (ms / 1e3), "unit": "vertex queries/s", "D": float(r[0]),
+            "rel_diff_vs_whole_body_reduce": {
+                "D": float(abs(r[0] - whole[0]) / max(abs(whole[0]), 1e-2)),
+                "gradient": float(np.linalg.norm(r[1:] - whole[1:]) / max(np.linalg.norm(whole[1:]), 1e-2))}}
+
+
+def _cpu_baseline(c, args, sample=None, min_seconds=0.0, single_thread=True):
     """The FP64 oracle as it stands on this host's cores: its own tree build
     over the full mesh plus Barnes-Hut on a query sample (repeated until
     min_seconds of work); the rate is scaled to the full batch as
-    M / (t_build + t_query * M / sample)."""
+    M / (t_build + t_query * M / sample). With single_thread, also the same
+    Barnes-Hut on one thread over the first 8,192 queries (tree build
+    excluded)."""
     import oracle
     cores = oracle.default_threads()
     M = c["queries"].shape[0]
@@ -894,10 +1156,19 @@ def _cpu_baseline(c, args, sample=None, min_seconds=0.0):
     tb /= reps
     tq /= reps
     full = tb + tq * M / sample
-    return {"value": M / full, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{reps} x (oracle tree build over all 81,920 triangles ({tb:.2f} s) + FP64 Barnes-Hut on "
-                      f"{'all' if sample == M else f'the first {sample} of'} {M} queries ({tq:.2f} s, {cores} "
-                      f"threads)); mean per pass" + ("" if sample == M else ", rate scaled to the full batch")}
+    out = {"value": M / full, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": f"{reps} x (oracle tree build over all 81,920 triangles ({tb:.2f} s) + FP64 Barnes-Hut on "
+                     f"{'all' if sample == M else f'the first {sample} of'} {M} queries ({tq:.2f} s, {cores} "
+                     f"threads)); mean per pass" + ("" if sample == M else ", rate scaled to the full batch")}
+    if single_thread:
+        n1 = min(8192, M)
+        t0 = time.perf_counter()
+        sc.bh(c["queries"][:n1], args.alpha, args.beta, threads=1)
+        t1 = time.perf_counter() - t0
+        out["single_thread"] = {"value": n1 / t1, "unit": UNIT, "cores": 1,
+                                "sample": f"FP64 Barnes-Hut on the first {n1} queries, one thread, tree prebuilt "
+                                          f"({t1:.2f} s)"}
+    return out
 
 
 def run_reference(args):
@@ -910,10 +1181,9 @@ def run_reference(args):
     c = _workload(args, 0)
     cores = oracle.default_threads()
     M = c["queries"].shape[0]
-    sample = min(M, 4096 * cores)
     times = []
     for k in range(args.warmup + args.steps):
-        r = _cpu_baseline(c, args, sample=sample)
+        r = _cpu_baseline(c, args, sample=M, single_thread=False)
         if k >= args.warmup:
             times.append(M / r["value"])
     ms = 1e3 * sum(times) / len(times)
@@ -923,8 +1193,8 @@ def run_reference(args):
             "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded generators, synth/)",
             "config": _config(args, args.gpus), "impl": "reference",
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"per step: oracle tree build + Barnes-Hut on {sample} of {M} queries, "
-                                       f"scaled to the full batch"},
+                             "sample": f"per step: oracle tree build over all 81,920 triangles + FP64 "
+                                       f"Barnes-Hut on all {M} queries ({cores} threads), measured"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 

@@ -188,6 +188,36 @@ int sd_pose_reduce(const float* X0, const float* value, const float* grad, const
                    const double* pose, float alpha_q, float* out, float* dX0, void* stream);
 
 /*
+ * One shard of a body's vertices, for a reduction split across processes or
+ * GPUs (Sec. 3.6: the outer sum of Eq. lse_full2 and Eq. dlse_full is
+ * associative, so per-shard partials merge exactly up to rounding). Inputs
+ * as for sd_pose_reduce, restricted to the shard's vertices; writes device
+ * part[9] = (m, s, v, gp (3), gt (3)) with
+ *   alpha_q > 0:  t_k = -alpha_q d^_k, m = max_k t_k, e_k = exp(t_k - m);
+ *   alpha_q <= 0: m = 0, e_k = gamma_k (device [M]);
+ *   s = sum e_k, v = sum e_k d^_k, gp = sum e_k g_k,
+ *   gt = sum e_k (R x0_k) x g_k,
+ * summed in a fixed order (deterministic). M = 0 writes the merge's neutral
+ * element (m = -inf, the rest 0). Uses stream-ordered temporary memory.
+ */
+int sd_pose_partial(const float* X0, const float* value, const float* grad, const float* gamma, int64_t M,
+                    const double* pose, float alpha_q, float* part, void* stream);
+
+/*
+ * Host-only (needs no GPU): merges n shard partials (host double [n,9] in
+ * sd_pose_partial's layout, any grouping and order) and finalises them as
+ * sd_pose_reduce does, in FP64: out[7] = (D, dD/dp (3), dD/dtheta (3)) with
+ * M = max_i m_i, and S, V, GP, GT the shards' s, v, gp, gt scaled by
+ * exp(m_i - M) and summed:
+ *   alpha_q > 0:  D = -(M + log S)/alpha_q, dD/dp = GP/S,
+ *                 dD/dtheta = J_l(theta)^T GT/S;
+ *   alpha_q <= 0: D = V, dD/dp = GP, dD/dtheta = J_l(theta)^T GT.
+ * SD_ERR_INVALID_ARG for n <= 0, a NULL pointer, or (alpha_q > 0) only
+ * empty shards; SD_ERR_NONFINITE for a non-finite pose.
+ */
+int sd_pose_merge(const double* parts, int32_t n, const double* pose, float alpha_q, double* out);
+
+/*
  * Batched rigid bodies against one data mesh (the multi-object evaluation
  * behind Sec. 4.5's simulations): B bodies with uneven vertex counts,
  * flattened into one vertex list. sd_batch_run places every vertex from a
@@ -396,6 +426,23 @@ const char* sd_last_error(void);
  * order i = 7..0 outer, j = 7-i..0 inner. Needs no GPU.
  */
 int sd_weight_basis(double* out);
+
+/*
+ * Pipe-throughput probe (a measurement aid; the paper has no counterpart).
+ * The traversal is bound by the FP32 pipe with the MUFU (special-function)
+ * pipe as a co-bound; this measures both rates at whatever clock the GPU
+ * runs, as the roofline's denominators.
+ *   kind   0: fma.rn.f32; 1: fma.rn.f32x2 (two FMAs per lane and
+ *          instruction); 2: ex2.approx.ftz.f32 (each followed by one FMA on
+ *          the FP32 pipe that keeps the chain bounded)
+ *   blocks > 0 blocks of 256 threads; each thread runs iters x 16 steps of
+ *          8 independent dependency chains
+ *   sink   device [blocks*256] float32 output (keeps the chains live)
+ *   ops    host: lane operations of the launch (FMAs, or exponentials)
+ * Asynchronous on `stream`: time the launch with CUDA events. An FMA is
+ * 2 flops. SD_ERR_INVALID_ARG for an unknown kind or a non-positive size.
+ */
+int sd_peak_probe(int32_t kind, int32_t blocks, int32_t iters, float* sink, double* ops, void* stream);
 
 #ifdef __cplusplus
 }

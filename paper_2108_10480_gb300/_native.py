@@ -79,6 +79,9 @@ SIGNATURES = {
                                      ctypes.POINTER(SdQueryOpts), c_void_p]),
     "sd_pose_reduce": (ctypes.c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_void_p, c_float,
                                       c_void_p, c_void_p, c_void_p]),
+    "sd_pose_partial": (ctypes.c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_void_p, c_float,
+                                       c_void_p, c_void_p]),
+    "sd_pose_merge": (ctypes.c_int, [c_void_p, c_int32, c_void_p, c_float, c_void_p]),
     "sd_batch_create": (ctypes.c_int, [c_void_p, c_void_p, c_void_p, c_int32, ctypes.POINTER(c_void_p)]),
     "sd_batch_set_poses": (ctypes.c_int, [c_void_p, c_void_p, c_void_p]),
     "sd_batch_run": (ctypes.c_int, [c_void_p, c_float, c_int32, c_void_p, c_void_p]),
@@ -108,6 +111,7 @@ SIGNATURES = {
     "sd_status_str": (ctypes.c_char_p, [ctypes.c_int]),
     "sd_last_error": (ctypes.c_char_p, []),
     "sd_weight_basis": (ctypes.c_int, [c_void_p]),
+    "sd_peak_probe": (ctypes.c_int, [c_int32, c_int32, c_int32, c_void_p, ctypes.POINTER(c_double), c_void_p]),
 }
 
 _lib = None

@@ -29,11 +29,12 @@ struct PoseF {
     float J[9];   // row-major left Jacobian J_l(theta)
 };
 
-void pose_from_vector(const double* pose, PoseF& P)
+// R(theta) (Rodrigues) and the left Jacobian J_l(theta) in FP64, row-major
+void pose_matrices(const double* pose, double* R, double* J)
 {
     const double tx = pose[0], ty = pose[1], tz = pose[2];
     const double th = std::sqrt(tx * tx + ty * ty + tz * tz);
-    // Rodrigues: R = I + a [t]x + b [t]x^2, J_l = I + b [t]x + c [t]x^2
+    // R = I + a [t]x + b [t]x^2, J_l = I + b [t]x + c [t]x^2
     double a, b, c;
     if (th < 1e-4) {
         const double t2 = th * th;
@@ -55,8 +56,18 @@ void pose_from_vector(const double* pose, PoseF& P)
         }
     for (int i = 0; i < 9; ++i) {
         const double I = (i % 4 == 0) ? 1.0 : 0.0;
-        P.R[i] = (float)(I + a * K[i] + b * K2[i]);
-        P.J[i] = (float)(I + b * K[i] + c * K2[i]);
+        R[i] = I + a * K[i] + b * K2[i];
+        J[i] = I + b * K[i] + c * K2[i];
+    }
+}
+
+void pose_from_vector(const double* pose, PoseF& P)
+{
+    double R[9], J[9];
+    pose_matrices(pose, R, J);
+    for (int i = 0; i < 9; ++i) {
+        P.R[i] = (float)R[i];
+        P.J[i] = (float)J[i];
     }
     for (int j = 0; j < 3; ++j) P.p[j] = (float)pose[3 + j];
 }
@@ -238,6 +249,78 @@ extern "C" int sd_pose_reduce(const float* X0, const float* value, const float* 
     e = cudaGetLastError();
     cudaFreeAsync(tmp, st);
     return sd_cuda_status(e);
+}
+
+// One shard of a body's vertices (Sec. 3.6, the outer sum of Eq. lse_full2 /
+// Eq. dlse_full is associative): its LSE-shifted partial (m, s, v, sum e g,
+// sum e (R x0) x g) with e = exp(t_k - m), written to part[9] on the device.
+namespace {
+
+__global__ void k_pose_part_final(const Part* __restrict__ parts, int nparts, float* __restrict__ out)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    Part r = parts[0];
+    for (int b = 1; b < nparts; ++b) part_merge(r, parts[b]);
+    out[0] = r.m; out[1] = r.s; out[2] = r.v;
+    for (int j = 0; j < 3; ++j) { out[3 + j] = r.gp[j]; out[6 + j] = r.gt[j]; }
+}
+
+}  // namespace
+
+extern "C" int sd_pose_partial(const float* X0, const float* value, const float* grad, const float* gamma,
+                               int64_t M, const double* pose, float alpha_q, float* part, void* stream)
+{
+    if (!pose || !part || M < 0 || (M > 0 && (!X0 || !value || !grad))) return SD_ERR_INVALID_ARG;
+    if (!(alpha_q > 0.f) && M > 0 && !gamma) return SD_ERR_INVALID_ARG;
+    if (M >= ((int64_t)1 << 31) / 3) return SD_ERR_TOO_LARGE;
+    for (int j = 0; j < 6; ++j)
+        if (!std::isfinite(pose[j])) return SD_ERR_NONFINITE;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (M == 0) {
+        // the empty shard: the merge's neutral element
+        const float empty[9] = {-INFINITY, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        return sd_cuda_status(cudaMemcpyAsync(part, empty, sizeof(empty), cudaMemcpyHostToDevice, st));
+    }
+    PoseF P;
+    pose_from_vector(pose, P);
+    int m = (int)M;
+    int nparts = std::min((m + RB - 1) / RB, 1024);
+    void* tmp = nullptr;
+    cudaError_t e = cudaMallocAsync(&tmp, sizeof(Part) * nparts, st);
+    if (e != cudaSuccess) { cudaGetLastError(); return SD_ERR_OOM; }
+    k_pose_partials<<<nparts, RB, 0, st>>>(X0, value, grad, gamma, m, alpha_q, P, (Part*)tmp);
+    k_pose_part_final<<<1, 32, 0, st>>>((const Part*)tmp, nparts, part);
+    sd_count_launches(2);
+    e = cudaGetLastError();
+    cudaFreeAsync(tmp, st);
+    return sd_cuda_status(e);
+}
+
+extern "C" int sd_pose_merge(const double* parts, int32_t n, const double* pose, float alpha_q, double* out)
+{
+    if (!parts || n <= 0 || !pose || !out) return SD_ERR_INVALID_ARG;
+    for (int j = 0; j < 6; ++j)
+        if (!std::isfinite(pose[j])) return SD_ERR_NONFINITE;
+    const bool lse = alpha_q > 0.f;
+    double mx = -INFINITY;
+    for (int i = 0; i < n; ++i)
+        if (parts[9 * i + 1] > 0.0 && parts[9 * i] > mx) mx = parts[9 * i];
+    if (lse && !(mx > -INFINITY)) return SD_ERR_INVALID_ARG;    // every shard empty
+    double r[9] = {0.0};
+    for (int i = 0; i < n; ++i) {
+        const double* p = parts + 9 * i;
+        if (!(p[1] > 0.0) && lse) continue;                       // an empty shard adds nothing
+        const double e = lse ? std::exp(p[0] - mx) : 1.0;
+        for (int j = 1; j < 9; ++j) r[j] += p[j] * e;
+    }
+    double R[9], J[9];
+    pose_matrices(pose, R, J);
+    const double nrm = lse ? 1.0 / r[1] : 1.0;
+    out[0] = lse ? -(mx + std::log(r[1])) / (double)alpha_q : r[2];
+    for (int j = 0; j < 3; ++j) out[1 + j] = r[3 + j] * nrm;
+    for (int j = 0; j < 3; ++j)
+        out[4 + j] = (J[0 * 3 + j] * r[6] + J[1 * 3 + j] * r[7] + J[2 * 3 + j] * r[8]) * nrm;
+    return SD_OK;
 }
 
 // ---------------------------------------------------------------------------

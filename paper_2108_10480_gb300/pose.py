@@ -60,6 +60,50 @@ def pose_reduce(X0, value, grad, pose, alpha_q=None, gamma=None, want_dx0=False,
     return res, dX0
 
 
+def pose_partial(X0, value, grad, pose, alpha_q=None, gamma=None, stream=None):
+    """This shard's partial of the outer reduction (sd_pose_partial): device
+    float32 [9] = (m, s, v, gp (3), gt (3)) over the given vertices."""
+    M = value.shape[0]
+    part = torch.empty(9, device=value.device, dtype=torch.float32)
+    pa = _pose_array(pose)
+    aq = float(alpha_q) if alpha_q else 0.0
+    g = gamma.contiguous().to(torch.float32) if gamma is not None else None
+    rc = lib().sd_pose_partial(_ptr(X0), _ptr(value), _ptr(grad), _ptr(g) if g is not None else None, M,
+                               ctypes.c_void_p(pa.ctypes.data), aq, _ptr(part), _stream_handle(stream))
+    _native.check(rc, "sd_pose_partial")
+    return part
+
+
+def merge_partials(parts, pose, alpha_q=None):
+    """Merge shard partials (host [n, 9], any order) with the library's
+    host-only sd_pose_merge: float64 (D, dD/dtheta (3), dD/dp (3)), the pose
+    order of pose_reduce."""
+    P = np.ascontiguousarray(np.asarray(parts, np.float64).reshape(-1, 9))
+    pa = _pose_array(pose)
+    out = np.zeros(7, np.float64)
+    aq = float(alpha_q) if alpha_q else 0.0
+    rc = lib().sd_pose_merge(ctypes.c_void_p(P.ctypes.data), int(P.shape[0]), ctypes.c_void_p(pa.ctypes.data), aq,
+                             ctypes.c_void_p(out.ctypes.data))
+    _native.check(rc, "sd_pose_merge")
+    return np.concatenate([out[:1], out[4:7], out[1:4]])
+
+
+def reduce_shards(part, pose, alpha_q=None, group=None):
+    """The body's reduction when its vertices are split over the ranks of a
+    torch.distributed group: every rank's 9-float partial is all-gathered
+    (the one exchange of the split) and merged on the host by
+    sd_pose_merge. Without an initialised process group the partial is
+    merged alone."""
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        parts = [torch.empty_like(part) for _ in range(dist.get_world_size(group))]
+        dist.all_gather(parts, part, group=group)
+        host = torch.stack(parts).double().cpu().numpy()
+    else:
+        host = part.double().cpu().numpy()[None]
+    return merge_partials(host, pose, alpha_q)
+
+
 class SmoothDistancePose(torch.autograd.Function):
     """d^ of a rigid body against a built data mesh, differentiable in the
     6-DoF pose and the rest vertices."""

@@ -27,6 +27,8 @@ def _clocks(tmp_path, t0, lines):
     c.p = _Proc()
     c.f = open(str(tmp_path / "unused"), "w")
     c.t0 = t0
+    c.spans = {}
+    c.windows = {}
     return c
 
 
@@ -89,3 +91,42 @@ def test_reference_arm_json_line():
     assert d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
     assert d["e2e"]["value"] == d["value"] and d["e2e"]["unit"] == d["unit"]
+
+
+def test_window_of_a_named_span(tmp_path, monkeypatch):
+    now = time.time()
+    t0 = now - 1.0
+    lines = [_line(t0 - 3.0, 1500), _line(t0 - 2.5, 1600), _line(t0 + 0.5, 2070)]
+    c = _clocks(tmp_path, t0, lines)
+    c.spans["probe"] = [t0 - 3.1, t0 - 2.4]
+    monkeypatch.setattr(bench.time, "sleep", lambda s: None)
+    r = c.stop()
+    assert r["samples"] == 1 and r["sm_mhz"] == 2070.0
+    assert c.windows["probe"]["samples"] == 2 and c.windows["probe"]["sm_mhz"] == 1550.0
+
+
+def test_alu_roofline_uses_the_method_costs():
+    """frac = (tests x 20 + far x 12 + triangles x 160) flops / time / FP32
+    peak, the MUFU co-bound (far x 3 + triangles x 3) beside it; the larger
+    fraction names the binding pipe."""
+    peaks = {"fp32_tflops": 80.0, "mufu_gops": 5000.0}
+    w = {"test": 1000, "far": 500, "leaf": 40}
+    r = bench._alu_roofline(w, 1e-3, peaks, "tri")        # 1 us
+    flops = 1000 * 20 + 500 * 12 + 40 * 160
+    mufu = 500 * 3 + 40 * 3
+    assert r["work_per_launch"]["flops"] == flops and r["work_per_launch"]["mufu_ops"] == mufu
+    f32 = flops / 1e-6 / 1e12 / 80.0
+    fmu = mufu / 1e-6 / 1e9 / 5000.0
+    assert r["binding_pipe"] == ("fp32" if f32 >= fmu else "mufu")
+    assert abs(r["frac"] - max(f32, fmu)) < 1e-12 and abs(r["co_bound"]["frac"] - min(f32, fmu)) < 1e-12
+    # a MUFU-heavy unit mix binds on the MUFU pipe
+    r = bench._alu_roofline({"test": 0, "far": 1000, "leaf": 0}, 1e-3, {"fp32_tflops": 80.0, "mufu_gops": 100.0})
+    assert r["binding_pipe"] == "mufu" and r["unit"] == "Gop/s"
+    assert abs(r["frac"] - 3000 / 1e-6 / 1e9 / 100.0) < 1e-12
+
+
+def test_peaks_scale_with_the_clock():
+    p = {"fp32_tflops": 80.0, "mufu_gops": 5000.0}
+    s = bench._scale_peaks(p, 2000.0, 1500.0)
+    assert abs(s["fp32_tflops"] - 60.0) < 1e-12 and abs(s["mufu_gops"] - 3750.0) < 1e-9
+    assert bench._scale_peaks(p, None, 1500.0)["fp32_tflops"] == 80.0

@@ -118,3 +118,39 @@ def test_pose_full_street():
     sc = oracle.Scene(points=s["points"], edge_V=s["wire_V"], edge_E=s["wire_E"])
     sc.build_tree(1)
     _check(sd, sc, b["V0"], pose, 50.0, 100.0, 0.5)
+
+
+def test_sharded_reduction_matches_the_whole_body(small_street):
+    """Sec. 3.6's outer sum split into shards: sd_pose_partial on uneven
+    slices of the body's vertices (one of them empty), merged on the host by
+    sd_pose_merge, equals sd_pose_reduce over the whole body and the FP64
+    oracle, in the LSE mode and in the upstream-gradient (linear) mode."""
+    from paper_2108_10480_gb300 import SmoothDistance
+    from paper_2108_10480_gb300 import pose as gp
+    P, Vw, Ew, X0 = small_street
+    sc = oracle.Scene(points=P, edge_V=Vw, edge_E=Ew)
+    sd = SmoothDistance(points=P, edges=(Vw, Ew), alpha=5.0, beta=0.0, device="cuda:0")
+    pose = np.array([0.4, -0.3, 1.1, 20.0, 5.5, 6.0])
+    X0t = torch.from_numpy(X0).cuda()
+    X, v, g = gp.pose_query(sd, X0t, pose)
+    M = X0.shape[0]
+    cuts = [0, 7, 7, M // 3, M - 1, M]
+    whole, _ = gp.pose_reduce(X0t, v, g, pose, alpha_q=10.0)
+    whole = whole.cpu().numpy().astype(np.float64)
+    parts = np.stack([gp.pose_partial(X0t[a:b], v[a:b], g[a:b], pose, alpha_q=10.0).cpu().numpy()
+                      for a, b in zip(cuts[:-1], cuts[1:])])
+    assert parts[1, 0] == -np.inf and not parts[1, 1:].any()        # the empty shard
+    for order in (slice(None), slice(None, None, -1)):
+        r = gp.merge_partials(parts[order], pose, alpha_q=10.0)
+        assert abs(r[0] - whole[0]) <= 1e-6 * max(abs(whole[0]), 0.1), (r[0], whole[0])
+        assert _vec_err(r[1:], whole[1:]) <= 1e-5
+    D, G, _, _, _ = PO.pose_objective(sc, X0, pose, 5.0, 10.0, precision="f32")
+    assert abs(r[0] - D) / max(abs(D), 0.1) <= 1e-5 and _vec_err(r[1:], G) <= 1e-4
+    # linear mode: an upstream gradient gamma per vertex
+    w = torch.linspace(-1.0, 2.0, M, device="cuda")
+    lin, _ = gp.pose_reduce(X0t, v, g, pose, gamma=w)
+    parts = np.stack([gp.pose_partial(X0t[a:b], v[a:b], g[a:b], pose, gamma=w[a:b]).cpu().numpy()
+                      for a, b in zip(cuts[:-1], cuts[1:])])
+    r = gp.merge_partials(parts, pose)
+    lin = lin.cpu().numpy().astype(np.float64)
+    assert _vec_err(r[1:], lin[1:]) <= 1e-5 and abs(r[0] - lin[0]) <= 1e-5 * max(abs(lin[0]), 1.0)
