@@ -37,7 +37,9 @@ typedef enum {
     SD_ERR_NONFINITE = 4,   /* a vertex or query coordinate is NaN/Inf */
     SD_ERR_INDEX = 5,       /* an edge/triangle index is outside its vertex array */
     SD_ERR_TOO_LARGE = 6,   /* a size exceeds what the library supports (2^31-1 primitives) */
-    SD_ERR_TIMEOUT = 7      /* a bounded device-side wait ran out (the results of that call are invalid) */
+    SD_ERR_TIMEOUT = 7      /* a bounded device-side wait ran out (the results of that call are invalid);
+                               no entry point returns it at present: the sorts' waits fall back to an
+                               exact direct count, and the tensor-core kernel marks its rows NaN */
 } sd_status;
 
 /* Geometry of the data mesh M_d = (V, F) (Sec. 3). Each part may be empty
@@ -255,11 +257,14 @@ void sd_batch_free(sd_batch* b);
  * frame = host float[7] = (c_x, c_y, c_z, h_x, h_y, h_z, s): box centre,
  * half extents (> 0) and output scale; SD_ERR_INVALID_ARG otherwise.
  *   sd_mlp_forward: device x [n,3] -> y [n] and, if dydx is not NULL,
- *     dy/dx [n,3] (tcgen05 tensor-core kernel, one CTA with 219 KB of shared
+ *     dy/dx [n,3] (tcgen05 tensor-core kernel, one CTA with 224,176 bytes (218.9 KiB) of shared
  *     memory and all 512 tensor-memory columns per SM; features, a1, a2 and
  *     the back-propagated factors rounded to bfloat16, dsilu(z1), dsilu(z2)
- *     to binary16; input gradient by back-propagation). A tile whose
- *     tensor-core work does not complete (a bounded wait) gets NaN outputs.
+ *     to binary16; input gradient by back-propagation). If a bounded wait
+ *     for a 128-query tile's tensor-core work runs out, that tile and every
+ *     later tile of its warp group get NaN outputs: the group issues no
+ *     more work and waits (bounded) for what it already committed before
+ *     the tensor memory is freed.
  *   sd_mlp_train_step: one mean-squared-error step on a device batch
  *     (x [n,3], target [n]): writes loss (device [1]) and the gradient
  *     (device [num_params], zero for B); if lr > 0 also an Adam step (step
@@ -334,8 +339,8 @@ int sd_query_prims(const sd_tree* t, const float* QV, int64_t nqv, const int32_t
  *   out    device [1]: D = -(1/alpha_q) log sum_j exp(-alpha_q d^_j)
  *   vgrad  device [nqv,3] (may be NULL): dD/dv_k; vertices used by no
  *          primitive get 0; indices outside [0, nqv) are ignored
- *   status device int (may be NULL): SD_ERR_TIMEOUT's bit is or-ed in if a
- *          bounded wait of the vertex sort ran out
+ *   status device int (may be NULL): never written (kept for the ABI; the
+ *          vertex sort's bounded waits fall back to an exact direct count)
  * Sums run in a fixed order (deterministic). Asynchronous; uses
  * stream-ordered temporary memory.
  */

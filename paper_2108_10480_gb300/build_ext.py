@@ -29,25 +29,31 @@ def _nvcc() -> str:
     raise RuntimeError("nvcc not found: the CUDA library cannot be built")
 
 
-def _stale() -> bool:
-    if not os.path.exists(LIB):
+def _stale(lib=LIB) -> bool:
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     deps = [os.path.join(CSRC, s) for s in SOURCES + HEADERS] + [os.path.join(INCLUDE, "sd.h"), __file__]
     return any(os.path.getmtime(d) > t for d in deps if os.path.exists(d))
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    if not force and not _stale():
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, tag: str = "", defines=()) -> str:
+    """Build libsd.so; with a tag, a separate library _build/libsd_<tag>.so
+    compiled with the extra -D `defines` (test-only builds, e.g. with the
+    device-side wait limits lowered)."""
+    lib = os.path.join(BUILD, f"libsd_{tag}.so") if tag else LIB
+    objdir = os.path.join(BUILD, tag) if tag else BUILD
+    if not force and not _stale(lib):
+        return lib
+    os.makedirs(objdir, exist_ok=True)
     nvcc = _nvcc()
     common = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
+    common += ["-D" + d for d in defines]
     procs = []
     objs = []
     for s in SOURCES:
         src = os.path.join(CSRC, s)
-        obj = os.path.join(BUILD, os.path.splitext(s)[0] + ".o")
+        obj = os.path.join(objdir, os.path.splitext(s)[0] + ".o")
         objs.append(obj)
         if s.endswith(".cu"):
             cmd = [nvcc] + ARCH + common + ["-c", src, "-o", obj]
@@ -63,13 +69,13 @@ def build(force: bool = False, verbose: bool = False) -> str:
             failed.append((" ".join(cmd), out.decode(errors="replace")))
     if failed:
         raise RuntimeError("libsd build failed:\n" + "\n".join(f"$ {c}\n{o}" for c, o in failed))
-    tmp = LIB + f".{os.getpid()}.tmp"
+    tmp = lib + f".{os.getpid()}.tmp"
     cmd = [nvcc] + ARCH + ["-shared", "-cudart", "shared", "-o", tmp] + objs
     r = subprocess.run(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)
     if r.returncode != 0:
         raise RuntimeError("libsd link failed:\n" + r.stdout.decode(errors="replace"))
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

@@ -18,7 +18,7 @@
 
 namespace {
 
-enum { ST_NONFINITE = 1, ST_INDEX = 2, ST_TIMEOUT = 4 };
+enum { ST_NONFINITE = 1, ST_INDEX = 2 };
 
 // scalars the build accumulates on the device
 struct BuildScalars {
@@ -317,8 +317,8 @@ __global__ void k_karras(const unsigned long long* __restrict__ sk, const int* _
 }
 
 // write child slot `slot` of record `rec` (interleaved AABB with negated upper
-// corner, squared diagonal) and the child's far-field mass
-__device__ __forceinline__ void write_slot(SdNode* nodes, float2* nw2, int rec, int slot, const float* lo,
+// corner, squared diagonal) and log2 of the child's far-field mass
+__device__ __forceinline__ void write_slot(SdNode* nodes, float2* lw2, int rec, int slot, const float* lo,
                                            const float* hi, float nw)
 {
     float* r = reinterpret_cast<float*>(&nodes[rec]);
@@ -329,8 +329,8 @@ __device__ __forceinline__ void write_slot(SdNode* nodes, float2* nw2, int rec, 
     r[8 + slot] = -hi[1];
     r[10 + slot] = -hi[2];
     r[14 + slot] = box_diag2(lo, hi);
-    float* w = reinterpret_cast<float*>(&nw2[rec]);
-    w[slot] = nw;
+    float* w = reinterpret_cast<float*>(&lw2[rec]);
+    w[slot] = log2f(nw);
 }
 
 // Bottom-up aggregates: a thread per bucket computes the bucket's AABB over
@@ -341,7 +341,7 @@ __global__ void k_aggregate(Geo g, const int* __restrict__ sorted, int L, int nb
                             const int* __restrict__ right, const int* __restrict__ parent_int,
                             const int* __restrict__ parent_leaf, float* node_box, int* node_count, int* node_pts,
                             float* leaf_box, int* leaf_count, int* leaf_pts, int* visits, SdNode* nodes,
-                            float2* nw2, const BuildScalars* bs, float S, int unit)
+                            float2* lw2, const BuildScalars* bs, float S, int unit)
 {
     int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= nb) return;
@@ -369,10 +369,10 @@ __global__ void k_aggregate(Geo g, const int* __restrict__ sorted, int L, int nb
     leaf_pts[b] = pts;
     float nw = pts ? (float)count : __fmul_rn((float)count, wfar);
     int par = nb > 1 ? parent_leaf[b] : -1;
-    if (par < 0) { write_slot(nodes, nw2, nb - 1, 0, lo, hi, nw); return; }
+    if (par < 0) { write_slot(nodes, lw2, nb - 1, 0, lo, hi, nw); return; }
     int from = -(b + 1);        // the child this thread arrives from
     int lr = __ldg(&left[par]), rr = __ldg(&right[par]);
-    write_slot(nodes, nw2, par, lr == from ? 0 : 1, lo, hi, nw);
+    write_slot(nodes, lw2, par, lr == from ? 0 : 1, lo, hi, nw);
     int node = par;
     // Up the tree: the second thread to reach a node merges its own child's
     // aggregates (still in registers) with the sibling's, which the first
@@ -405,8 +405,8 @@ __global__ void k_aggregate(Geo g, const int* __restrict__ sorted, int L, int nb
         node_count[node] = count;
         node_pts[node] = pts;
         const float nnw = pts ? (float)count : __fmul_rn((float)count, wfar);
-        if (pp < 0) { write_slot(nodes, nw2, nb - 1, 0, lo, hi, nnw); return; }
-        write_slot(nodes, nw2, pp, plr == node ? 0 : 1, lo, hi, nnw);
+        if (pp < 0) { write_slot(nodes, lw2, nb - 1, 0, lo, hi, nnw); return; }
+        write_slot(nodes, lw2, pp, plr == node ? 0 : 1, lo, hi, nnw);
         from = node;
         lr = plr;
         rr = prr;
@@ -414,7 +414,7 @@ __global__ void k_aggregate(Geo g, const int* __restrict__ sorted, int L, int nb
     }
 }
 
-__global__ void k_super_root(SdNode* nodes, float2* nw2, int nb)
+__global__ void k_super_root(SdNode* nodes, float2* lw2, int nb)
 {
     SdNode& r = nodes[nb - 1];
     r.d.x = nb > 1 ? 0 : -1;
@@ -422,7 +422,7 @@ __global__ void k_super_root(SdNode* nodes, float2* nw2, int nb)
     float* f = reinterpret_cast<float*>(&r);
     for (int j = 1; j < 12; j += 2) f[j] = 0.f;   // slot 1 is empty
     f[15] = 0.f;
-    nw2[nb - 1].y = 0.f;
+    lw2[nb - 1].y = 0.f;   // (the empty slot is never tested)
 }
 
 // the tree's scalars from the build's atomics (one thread): weight scales,
@@ -449,7 +449,6 @@ __global__ void k_finalize(const BuildScalars* bs, int unit, SdScalars* sc, int*
     sc->A_T = unit ? 1.f : (float)bs->A_T;
     sc->status = bs->status;
     if (bs->status & ST_INDEX) atomicOr(status, 1 << SD_ERR_INDEX);
-    if (bs->status & ST_TIMEOUT) atomicOr(status, 1 << SD_ERR_TIMEOUT);
     if (bs->status & ST_NONFINITE) atomicOr(status, 1 << SD_ERR_NONFINITE);
 }
 
@@ -631,7 +630,7 @@ extern "C" int sd_build(const sd_geometry* g, float alpha, float beta, const sd_
     if (ce != cudaSuccess) { delete t; cudaGetLastError(); return SD_ERR_OOM; }
     char* base = (char*)t->mem;
     t->nodes = (SdNode*)(base + o_nodes);
-    t->nw2 = (float2*)(base + o_nw);
+    t->lw2 = (float2*)(base + o_nw);
     t->hdr = (float4*)(base + o_hdr);
     t->ext = (float4*)(base + o_ext);
     t->codes = (uint64_t*)(base + o_codes);
@@ -764,8 +763,7 @@ extern "C" int sd_build(const sd_geometry* g, float alpha, float beta, const sd_
         // Morton order
         ++nl;
         k_morton<<<nblk(n, T), T, 0, st>>>(geo, bs, (unsigned long long*)t->codes, k0, v0);
-        int where = sdsort::sort_pairs<unsigned long long, int>(k0, v0, k1, v1, n, 64, hist, &bs->status,
-                                                                 ST_TIMEOUT, st, &nl);
+        int where = sdsort::sort_pairs<unsigned long long, int>(k0, v0, k1, v1, n, 64, hist, st, &nl);
         unsigned long long* sk = where ? k1 : k0;
         int* sv = where ? v1 : v0;
         // the gather needs the sorted order and the parameters
@@ -782,13 +780,13 @@ extern "C" int sd_build(const sd_geometry* g, float alpha, float beta, const sd_
             k_karras<<<nblk(nb - 1, T), T, 0, st>>>(sk, sv, L, nb, t->left, t->right, pint, pleaf, t->nodes);
         }
         ++nl;
-        k_super_root<<<1, 1, 0, st>>>(t->nodes, t->nw2, nb);
+        k_super_root<<<1, 1, 0, st>>>(t->nodes, t->lw2, nb);
         // aggregates (far-field weights use A)
         if (ps != st) cudaStreamWaitEvent(st, ev_params, 0);
         ++nl;
         k_aggregate<<<nblk(nb, T), T, 0, st>>>(geo, sv, L, nb, t->left, t->right, pint, pleaf, t->node_box,
                                                 t->node_count,
-                                                npts, t->leaf_box, t->leaf_count, lpts, visits, t->nodes, t->nw2,
+                                                npts, t->leaf_box, t->leaf_count, lpts, visits, t->nodes, t->lw2,
                                                 bs, S, t->weights_unit);
         if (ps != st) cudaStreamWaitEvent(st, ev_gather, 0);
     }
@@ -827,7 +825,6 @@ extern "C" int sd_build(const sd_geometry* g, float alpha, float beta, const sd_
         if (ce != cudaSuccess) status = sd_cuda_status(ce);
         else if (hs.status & ST_INDEX) status = SD_ERR_INDEX;
         else if (hs.status & ST_NONFINITE) status = SD_ERR_NONFINITE;
-        else if (hs.status & ST_TIMEOUT) status = SD_ERR_TIMEOUT;
         if (status != SD_OK) {
             cudaFreeAsync(t->mem, st);
             delete t;
@@ -847,7 +844,7 @@ extern "C" int sd_build(const sd_geometry* g, float alpha, float beta, const sd_
         return wrc;
     }
     P.nodes = t->nodes;
-    P.nw2 = t->nw2;
+    P.lw2 = t->lw2;
     P.hdr = t->hdr;
     P.ext = t->ext;
     P.root_record = nb - 1;

@@ -21,7 +21,7 @@
 //   c = (-c0.hi.y, -c1.hi.y, -c0.hi.z, -c1.hi.z)
 //   d = (ref0, ref1, bits(diag2_0), bits(diag2_1))
 // ref >= 0: internal node; ref < 0: leaf bucket -(ref + 1); SD_NO_CHILD: none.
-// The far-field masses n_B w_B of both children sit in nw2[record].
+// log2 of the far-field masses n_B w_B of both children sits in lw2[record].
 struct __align__(16) SdNode {
     float4 a, b, c;
     int4 d;
@@ -49,7 +49,7 @@ struct SdScalars {
 // Parameters a traversal needs, passed by value to the kernels.
 struct SdParams {
     const SdNode* nodes;
-    const float2* nw2;    // far-field masses of both children, per record
+    const float2* lw2;    // log2 of the far-field masses n_B w_B of both children, per record
     const float4* hdr;
     const float4* ext;
     int root_record;      // nb - 1 (also the offset of bucket ids in nw)
@@ -82,7 +82,7 @@ struct sd_tree {
     void* mem;
     size_t mem_bytes;
     SdNode* nodes;        // nb records (nb - 1 internal + super-root)
-    float2* nw2;          // nb pairs of far-field masses
+    float2* lw2;          // nb pairs of log2 far-field masses
     float4* hdr;          // n
     float4* ext;          // 2n (only when edges or triangles exist)
     uint64_t* codes;      // n, original order

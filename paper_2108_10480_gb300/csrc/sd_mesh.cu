@@ -142,9 +142,7 @@ extern "C" int sd_mesh_reduce(const int32_t* QF, int32_t k, int64_t M, int64_t n
         uint32_t* hist = (uint32_t*)(b + o_hist);
         cudaMemsetAsync(first, 0, sizeof(int) * 2 * (size_t)nv, st);
         k_mesh_slots<<<(n + 255) / 256, 256, 0, st>>>(QF, n, nv, k0, s0);
-        int* err = status ? status : last + nv;
-        int where = sdsort::sort_pairs<unsigned, int>(k0, s0, k1, s1, n, bits, hist, err, 1 << SD_ERR_TIMEOUT, st,
-                                                      &nl);
+        int where = sdsort::sort_pairs<unsigned, int>(k0, s0, k1, s1, n, bits, hist, st, &nl);
         const unsigned* sk = where ? k1 : k0;
         const int* sv = where ? s1 : s0;
         k_mesh_bounds<<<(n + 255) / 256, 256, 0, st>>>(sk, n, nv, first, last);

@@ -246,7 +246,14 @@ constexpr int F_BIAS = 0, F_BQ = 4 * HID, F_B4 = F_BQ + 96, F_YP = F_B4 + 4, F_G
 constexpr int O_BAR = O_F32 + 4 * F_END;
 constexpr size_t TC_SMEM = (size_t)O_BAR + 32;    // 2 mbarriers, TMEM address, 2 wait flags
 static_assert(O_X % 1024 == 0 && O_BAR % 8 == 0 && TC_SMEM <= 232448, "tcgen05 MLP shared memory layout");
-constexpr int TC_WAIT_LIMIT = 1 << 24;  // mbarrier polls before a tile is abandoned (outputs NaN)
+// mbarrier polls before a tile is abandoned (its group's remaining outputs
+// become NaN), and polls of the drain that then waits for the GEMMs already
+// issued before the tensor memory is freed
+#ifndef SD_TC_WAIT_LIMIT
+#define SD_TC_WAIT_LIMIT (1 << 24)
+#endif
+constexpr int TC_WAIT_LIMIT = SD_TC_WAIT_LIMIT;
+constexpr int TC_DRAIN_LIMIT = 1 << 24;
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p)
 {
@@ -317,10 +324,10 @@ __device__ __forceinline__ void tc_commit(uint32_t bar)
 }
 
 // bounded wait for the mbarrier phase with parity `ph`
-__device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t ph)
+__device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t ph, int limit)
 {
     uint32_t done = 0;
-    for (int it = 0; it < TC_WAIT_LIMIT && !done; ++it)
+    for (int it = 0; it < limit && !done; ++it)
         asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
                      : "=r"(done) : "r"(bar), "r"(ph));
     return done != 0;
@@ -401,14 +408,6 @@ __device__ __forceinline__ void group_sync(int g)
     asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "r"(TC_GROUP));
 }
 
-__device__ __forceinline__ bool group_all(int g, bool p)
-{
-    uint32_t r;
-    asm volatile("{\n.reg .pred q, o;\nsetp.ne.u32 q, %1, 0;\nbar.red.and.pred o, %2, %3, q;\nselp.u32 %0, 1, 0, o;\n}\n"
-                 : "=r"(r) : "r"((uint32_t)p), "r"(1 + g), "r"(TC_GROUP));
-    return r != 0;
-}
-
 // make this thread's shared-memory and TMEM writes visible to the next
 // tensor-core operation of the group, then hand the issue to its thread 0
 __device__ __forceinline__ void tc_sync_before_mma(int g)
@@ -424,7 +423,7 @@ __device__ __forceinline__ void tc_sync_before_mma(int g)
 // other group); returns whether the GEMMs completed
 __device__ __forceinline__ bool group_wait(int g, bool issuer, uint32_t bar, uint32_t ph, volatile int* flag)
 {
-    if (issuer) *flag = bar_wait(bar, ph) ? 1 : 0;
+    if (issuer) *flag = bar_wait(bar, ph, TC_WAIT_LIMIT) ? 1 : 0;
     group_sync(g);
     const bool ok = *flag != 0;
     asm volatile("tcgen05.fence::after_thread_sync;");
@@ -530,7 +529,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mlp_tc(const float* __restric
             }
             st_bf16x8(X, core_off(row, half * 40 + fc * 8, KF1), f);
         }
-        bool ok = true;
         // forward: layers 1..3
 #pragma unroll 1
         for (int layer = 0; layer < 3; ++layer) {
@@ -540,7 +538,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mlp_tc(const float* __restric
                 else tc_gemm_fwd(tg, xa, layer == 1 ? w2a : w3a, HID, HID);
                 tc_commit(bar_a);
             }
-            ok = group_wait(g, issuer, bar_a, ph, wflag) && ok;
+            if (!group_wait(g, issuer, bar_a, ph, wflag)) goto tile_failed;
             ph ^= 1u;
             const float4* bb = reinterpret_cast<const float4*>(F32 + F_BIAS + layer * HID);
             const float4* w4v = reinterpret_cast<const float4*>(w4);
@@ -584,7 +582,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mlp_tc(const float* __restric
             if (layer == 2) {
                 if (half) yp_h[row] = yp;
                 group_sync(g);
-                if (!half && r < n) y[r] = ok ? fr.s * ((yp + yp_h[row]) + F32[F_B4]) : __int_as_float(0x7fffffff);
+                if (!half && r < n) y[r] = fr.s * ((yp + yp_h[row]) + F32[F_B4]);
             }
         }
         if (dydx) {
@@ -597,7 +595,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mlp_tc(const float* __restric
                     else tc_gemm_bwd(tg, xa, layer == 2 ? w3a : w2a, HID);
                     tc_commit(bar_a);
                 }
-                ok = group_wait(g, issuer, bar_a, ph, wflag) && ok;
+                if (!group_wait(g, issuer, bar_a, ph, wflag)) goto tile_failed;
                 ph ^= 1u;
                 if (layer > 0) {
 #pragma unroll 1
@@ -651,12 +649,26 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mlp_tc(const float* __restric
                     group_sync(g);
                     if (!half && r < n)
                         for (int j = 0; j < 3; ++j)
-                            dydx[3 * r + j] = ok ? (gg[j] + gp_h[3 * row + j]) / fr.h[j] : __int_as_float(0x7fffffff);
+                            dydx[3 * r + j] = (gg[j] + gp_h[3 * row + j]) / fr.h[j];
                 }
             }
         }
-        // a tile whose tensor-core work did not complete ends the group's walk
-        if (!group_all(g, ok)) break;
+        continue;
+    tile_failed:
+        // A wait ran out (the same verdict for the whole group): no further
+        // GEMM is issued, this tile's rows and those of every later tile of
+        // the group are NaN, and the issuing thread waits (bounded) for the
+        // GEMM already committed before the tensor memory is freed.
+        if (!half)
+            for (int tt = tile; tt < ntiles; tt += tstep) {
+                const int rr = tt * TM + row;
+                if (rr >= n) break;
+                y[rr] = __int_as_float(0x7fffffff);
+                if (dydx) dydx[3 * rr] = dydx[3 * rr + 1] = dydx[3 * rr + 2] = __int_as_float(0x7fffffff);
+            }
+        if (issuer) bar_wait(bar_a, ph, TC_DRAIN_LIMIT);
+        group_sync(g);
+        break;
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
@@ -842,7 +854,7 @@ __global__ void k_cut(SdParams P, const unsigned* __restrict__ kbits, CutNode* _
         const float* f = reinterpret_cast<const float*>(&P.nodes[rec]);
         c.lo[0] = f[0 + slot]; c.lo[1] = f[2 + slot]; c.lo[2] = f[4 + slot];
         c.hi[0] = -f[6 + slot]; c.hi[1] = -f[8 + slot]; c.hi[2] = -f[10 + slot];
-        c.w = slot ? P.nw2[rec].y : P.nw2[rec].x;
+        c.w = exp2f(slot ? P.lw2[rec].y : P.lw2[rec].x);
     };
     refs[0][0] = P.nodes[P.root_record].d.x;
     read(P.root_record, 0, nodes[0][0]);
@@ -1025,7 +1037,7 @@ extern "C" int sd_surrogate_query(const sd_tree* t, const float* params, const f
     k_iota_flagkey<<<(m + 255) / 256, 256, 0, st>>>(flag, m, k0, v0, cnt);
     int nl = 1;
     // stable partition: exact queries first, surrogate queries after
-    int where = sdsort::sort_pairs<unsigned, int>(k0, v0, k1, v1, m, 1, hist, t->status, 1 << SD_ERR_TIMEOUT, st, &nl);
+    int where = sdsort::sort_pairs<unsigned, int>(k0, v0, k1, v1, m, 1, hist, st, &nl);
     int* idx = where ? v1 : v0;
     int hcnt = 0;
     e = cudaMemcpyAsync(&hcnt, cnt, sizeof(int), cudaMemcpyDeviceToHost, st);

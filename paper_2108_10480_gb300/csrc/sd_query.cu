@@ -152,49 +152,83 @@ __device__ __forceinline__ void queue_leaf(const SdParams& P, float3 q, int qi, 
 
 // Both children of one record, for every lane of the packet at once. The two
 // Barnes-Hut tests run as packed two-wide fp32 operations whose per-element
-// rounding equals the scalar test (lo - q = lo + (-q), q - hi = q + (-hi));
-// both far-field terms of App. D (n_B w_B e^{-alpha d} with direction
-// (q - y_B)/d) are added without branches. Returns the lane masks of the
-// children that must be opened.
+// rounding equals the scalar test of the oracle (for a point query the
+// offset to the box's closest point is q + max(-max(q, lo), -hi), which is
+// exactly lo - q, q - hi or 0). Accepted far fields (App. D) add
+// n_B w_B e^{-alpha d} with direction (q - y_B)/d, the mass folded into the
+// base-2 exponent y = log2(n_B w_B) - alpha log2(e) d. The LogSumExp
+// reference m is raised only when a term would exceed it by more than
+// 2^LSE_HEADROOM (a rare warp-uniform branch), and a record whose far terms
+// all lie below 2^-LSE_DROP of the reference skips their arithmetic. The
+// term that set m contributes its weight to the running sum, at least 1 for
+// a far field and at least 6e-6 (w~ clamped at 1e-6) for a leaf term; with
+// at most ~10^4 terms dropped per query the dropped mass stays below
+// 10^4 * 2^-64 / 6e-6 < 10^-10 of the sum, far under fp32 resolution.
+// Returns the lane masks of the children that must be opened and whether
+// the packet should descend into child 1 first (the child nearer to most of
+// its lanes).
+constexpr float LSE_HEADROOM = 64.f;
+constexpr float LSE_DROP = 64.f;
+
 template <int KINDS, bool GRAD, bool COUNT, int QK>
 __device__ __forceinline__ void packet_record(const SdParams& P, float3 q, float3 nq3, int qi, const QPrims& QP,
-                                              bool mine, int rec, Lse& acc, const WarpShared& ws, int& nq, int lane,
-                                              int& ntest, int& nfar, int& nleaf, int& ref0, int& ref1,
-                                              unsigned& open0, unsigned& open1)
+                                              bool mine, unsigned mask, int rec, Lse& acc, const WarpShared& ws,
+                                              int& nq, int lane, int& ntest, int& nfar, int& nleaf, int& ref0,
+                                              int& ref1, unsigned& open0, unsigned& open1, bool& first1)
 {
     const SdNode& r = P.nodes[rec];
     float4 a = __ldg(&r.a), b = __ldg(&r.b), c = __ldg(&r.c);
     int4 d = __ldg(&r.d);
-    float2 nw = __ldg(&P.nw2[rec]);
+    const float2 lw = __ldg(&P.lw2[rec]);
     const bool has1 = d.y != SD_NO_CHILD;
-    float2 ax = __fadd2_rn(make_float2(a.x, a.y), make_float2(nq3.x, nq3.x));
-    float2 ay = __fadd2_rn(make_float2(a.z, a.w), make_float2(nq3.y, nq3.y));
-    float2 az = __fadd2_rn(make_float2(b.x, b.y), make_float2(nq3.z, nq3.z));
-    float2 bx = __fadd2_rn(make_float2(q.x, q.x), make_float2(b.z, b.w));
-    float2 by = __fadd2_rn(make_float2(q.y, q.y), make_float2(c.x, c.y));
-    float2 bz = __fadd2_rn(make_float2(q.z, q.z), make_float2(c.z, c.w));
-    float2 dx = make_float2(fmaxf(fmaxf(ax.x, bx.x), 0.f), fmaxf(fmaxf(ax.y, bx.y), 0.f));
-    float2 dy = make_float2(fmaxf(fmaxf(ay.x, by.x), 0.f), fmaxf(fmaxf(ay.y, by.y), 0.f));
-    float2 dz = make_float2(fmaxf(fmaxf(az.x, bz.x), 0.f), fmaxf(fmaxf(az.y, bz.y), 0.f));
-    float2 db = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
-    float2 rhs = __fmul2_rn(make_float2(P.beta2, P.beta2), db);
+    float2 ox, oy, oz;
+    if (QK == 1) {
+        ox = __fadd2_rn(make_float2(q.x, q.x), make_float2(fmaxf(-fmaxf(q.x, a.x), b.z), fmaxf(-fmaxf(q.x, a.y), b.w)));
+        oy = __fadd2_rn(make_float2(q.y, q.y), make_float2(fmaxf(-fmaxf(q.y, a.z), c.x), fmaxf(-fmaxf(q.y, a.w), c.y)));
+        oz = __fadd2_rn(make_float2(q.z, q.z), make_float2(fmaxf(-fmaxf(q.z, b.x), c.z), fmaxf(-fmaxf(q.z, b.y), c.w)));
+    } else {
+        // gap between the query primitive's box [q, -nq3] and the child box
+        // per axis, signed by the side the query lies on
+        float2 ax = __fadd2_rn(make_float2(a.x, a.y), make_float2(nq3.x, nq3.x));
+        float2 ay = __fadd2_rn(make_float2(a.z, a.w), make_float2(nq3.y, nq3.y));
+        float2 az = __fadd2_rn(make_float2(b.x, b.y), make_float2(nq3.z, nq3.z));
+        float2 bx = __fadd2_rn(make_float2(q.x, q.x), make_float2(b.z, b.w));
+        float2 by = __fadd2_rn(make_float2(q.y, q.y), make_float2(c.x, c.y));
+        float2 bz = __fadd2_rn(make_float2(q.z, q.z), make_float2(c.z, c.w));
+        ox = make_float2(copysignf(fmaxf(fmaxf(ax.x, bx.x), 0.f), bx.x), copysignf(fmaxf(fmaxf(ax.y, bx.y), 0.f), bx.y));
+        oy = make_float2(copysignf(fmaxf(fmaxf(ay.x, by.x), 0.f), by.x), copysignf(fmaxf(fmaxf(ay.y, by.y), 0.f), by.y));
+        oz = make_float2(copysignf(fmaxf(fmaxf(az.x, bz.x), 0.f), bz.x), copysignf(fmaxf(fmaxf(az.y, bz.y), 0.f), bz.y));
+    }
+    const float2 db = __ffma2_rn(oz, oz, __ffma2_rn(oy, oy, __fmul2_rn(ox, ox)));
+    const float2 rhs = __fmul2_rn(make_float2(P.beta2, P.beta2), db);
     const bool t1 = mine && has1;
     const bool far0 = mine && __int_as_float(d.z) < rhs.x;
     const bool far1 = t1 && __int_as_float(d.w) < rhs.y;
     {
         float r0 = rsqrtf(db.x), r1 = rsqrtf(db.y);
-        float y0 = far0 ? -P.alpha2 * (db.x * r0) : SD_NEG;
-        float y1 = far1 ? -P.alpha2 * (db.y * r1) : SD_NEG;
-        float w0 = far0 ? nw.x : 0.f;
-        float w1 = far1 ? nw.y : 0.f;
-        float3 v0 = f3(0.f, 0.f, 0.f), v1 = f3(0.f, 0.f, 0.f);
-        if (GRAD) {
-            r0 = far0 ? r0 : 0.f;
-            r1 = far1 ? r1 : 0.f;
-            v0 = f3(copysignf(dx.x, bx.x) * r0, copysignf(dy.x, by.x) * r0, copysignf(dz.x, bz.x) * r0);
-            v1 = f3(copysignf(dx.y, bx.y) * r1, copysignf(dy.y, by.y) * r1, copysignf(dz.y, bz.y) * r1);
+        float2 y = __ffma2_rn(make_float2(-P.alpha2, -P.alpha2), __fmul2_rn(db, make_float2(r0, r1)), lw);
+        y.x = far0 ? y.x : SD_NEG;
+        y.y = far1 ? y.y : SD_NEG;
+        const float ym = fmaxf(y.x, y.y);
+        if (__any_sync(0xffffffffu, ym > acc.m + LSE_HEADROOM)) {
+            const float mn = fmaxf(acc.m, ym);
+            const float e = sd_ex2(acc.m - mn);
+            acc.s *= e;
+            if (GRAD) { acc.gx *= e; acc.gy *= e; acc.gz *= e; }
+            acc.m = mn;
         }
-        lse_add2<GRAD>(acc, y0, w0, v0, y1, w1, v1);
+        if (__any_sync(0xffffffffu, ym > acc.m - LSE_DROP)) {
+            const float2 t = __fadd2_rn(y, make_float2(-acc.m, -acc.m));
+            const float c0 = far0 ? sd_ex2(t.x) : 0.f;
+            const float c1 = far1 ? sd_ex2(t.y) : 0.f;
+            acc.s += c0 + c1;
+            if (GRAD) {
+                const float2 cr = make_float2(far0 ? c0 * r0 : 0.f, far1 ? c1 * r1 : 0.f);
+                acc.gx = fmaf(cr.x, ox.x, fmaf(cr.y, ox.y, acc.gx));
+                acc.gy = fmaf(cr.x, oy.x, fmaf(cr.y, oy.y, acc.gy));
+                acc.gz = fmaf(cr.x, oz.x, fmaf(cr.y, oz.y, acc.gz));
+            }
+        }
     }
     if (COUNT) {
         ntest += mine ? (has1 ? 2 : 1) : 0;
@@ -204,6 +238,8 @@ __device__ __forceinline__ void packet_record(const SdParams& P, float3 q, float
     const bool near1 = t1 && !far1;
     const unsigned nm0 = __ballot_sync(0xffffffffu, near0);
     const unsigned nm1 = __ballot_sync(0xffffffffu, near1);
+    const unsigned p1 = __ballot_sync(0xffffffffu, mine && db.y < db.x);
+    first1 = 2 * __popc(p1) > __popc(mask);
     ref0 = d.x;
     ref1 = d.y;
     open0 = open1 = 0u;
@@ -285,18 +321,24 @@ __global__ void __launch_bounds__(PK_MAX_THREADS) k_traverse(SdParams P, const f
             const bool mine = (mask >> lane) & 1u;
             int r0, r1;
             unsigned o0, o1;
-            packet_record<KINDS, GRAD, COUNT, QK>(P, q, nq3, qi, QP, mine, rec, acc, ws, nq, lane, ntest, nfar,
-                                                  nleaf, r0, r1, o0, o1);
-            // descend into a child that must be opened; keep the other on the stack
+            bool first1;
+            packet_record<KINDS, GRAD, COUNT, QK>(P, q, nq3, qi, QP, mine, mask, rec, acc, ws, nq, lane, ntest,
+                                                  nfar, nleaf, r0, r1, o0, o1, first1);
+            // descend into a child that must be opened (the nearer one when
+            // both are, so that the LogSumExp reference settles early); keep
+            // the other on the stack
             if (o0) {
                 if (o1) {
                     if (sp < PK_STACK) {
-                        if (lane == 0) ws.stack[sp] = make_int2(r1, (int)o1);
+                        if (lane == 0) ws.stack[sp] = first1 ? make_int2(r0, (int)o0) : make_int2(r1, (int)o1);
                         ++sp;
                     } else {
                         overflow = true;
                         break;
                     }
+                    rec = first1 ? r1 : r0;
+                    mask = first1 ? o1 : o0;
+                    continue;
                 }
                 rec = r0;
                 mask = o0;
@@ -315,8 +357,15 @@ __global__ void __launch_bounds__(PK_MAX_THREADS) k_traverse(SdParams P, const f
             mask = (unsigned)e.y;
         }
         if (nq > 0) flush_queue<KINDS, GRAD, QK>(P, q, qi, QP, ws.queue, nq, ws, lane, acc);
-        if (overflow && lane == 0) atomicOr(status, 1 << SD_ERR_TOO_LARGE);
         if (!ok) continue;
+        if (overflow) {
+            // a walk deeper than the stack (no radix tree over 95-bit keys is):
+            // the packet's outputs are NaN, never a partial sum
+            if (lane == 0) atomicOr(status, 1 << SD_ERR_TOO_LARGE);
+            value[qi] = __int_as_float(0x7fffffff);
+            if (GRAD) grad[3 * qi] = grad[3 * qi + 1] = grad[3 * qi + 2] = __int_as_float(0x7fffffff);
+            continue;
+        }
         // Alg. 2: d^ = -log(c)/alpha, grad d^ = grad c / c (c >= 1 after the shift)
         value[qi] = -(acc.m + sd_lg2(acc.s)) * P.inv_alpha2;
         if (GRAD) {
@@ -557,8 +606,7 @@ int compute_order(const sd_tree* t, const float* q, int m, int32_t* order, cudaS
     // the sort's odd pass count leaves its result in the second buffer: give
     // it `order` there and start from the scratch copy
     k_query_codes<<<(m + 255) / 256, 256, 0, st>>>(q, m, t->sc, k0, v1);
-    int where = sdsort::sort_pairs<unsigned, int>(k0, v1, k1, order, m, 24, hist, t->status, 1 << SD_ERR_TIMEOUT,
-                                                  st, &nl);
+    int where = sdsort::sort_pairs<unsigned, int>(k0, v1, k1, order, m, 24, hist, st, &nl);
     if (!where) cudaMemcpyAsync(order, v1, sizeof(int) * (size_t)m, cudaMemcpyDeviceToDevice, st);
     sd_count_launches(nl);
     e = cudaGetLastError();
@@ -824,8 +872,7 @@ extern "C" int sd_query_noalloc(const sd_tree* t, const float* q, int64_t M, flo
     if (m > 1) {
         k_query_codes<<<(m + 255) / 256, 256, 0, st>>>(q, m, t->sc, k0, ord0);
         ++nl;
-        int where = sdsort::sort_pairs<unsigned, int>(k0, ord0, k1, ord1, m, 24, hist, t->status,
-                                                      1 << SD_ERR_TIMEOUT, st, &nl);
+        int where = sdsort::sort_pairs<unsigned, int>(k0, ord0, k1, ord1, m, 24, hist, st, &nl);
         order = where ? ord1 : ord0;
     }
     dispatch<false>(t, q, m, order, value, grad, nullptr, 0, work, st);
@@ -856,8 +903,7 @@ int order_into(const sd_tree* t, const float* q, int m, int32_t* order, void* sc
     // the sort's odd pass count leaves its result in the second buffer: give
     // it `order` there and start from the scratch copy
     k_query_codes<<<(m + 255) / 256, 256, 0, st>>>(q, m, t->sc, k0, v1);
-    int where = sdsort::sort_pairs<unsigned, int>(k0, v1, k1, order, m, 24, hist, t->status, 1 << SD_ERR_TIMEOUT,
-                                                  st, &nl);
+    int where = sdsort::sort_pairs<unsigned, int>(k0, v1, k1, order, m, 24, hist, st, &nl);
     if (!where) cudaMemcpyAsync(order, v1, sizeof(int) * (size_t)m, cudaMemcpyDeviceToDevice, st);
     sd_count_launches(nl);
     return sd_cuda_status(cudaGetLastError());

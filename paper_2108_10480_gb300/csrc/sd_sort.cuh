@@ -8,8 +8,10 @@
 // of primitives (64-bit keys) and of queries (32-bit keys).
 //
 // The look-back only waits on tiles with smaller indices, which were taken
-// by blocks that already run; every wait is bounded all the same, and a wait
-// that runs out sets the error word (the sort's result is then invalid).
+// by blocks that already run; every wait is bounded all the same. A tile
+// whose wait runs out counts its digit prefix directly instead (every key of
+// the earlier tiles, read from the pass's input): slower, but the same exact
+// prefix, so the sort's result never depends on the wait.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -27,7 +29,12 @@ constexpr int MAX_PASSES = 8;
 constexpr uint32_t FLAG_AGG = 1u << 30;     // the tile's own counts
 constexpr uint32_t FLAG_PRE = 2u << 30;     // counts of tiles 0..i inclusive
 constexpr uint32_t VALUE = FLAG_AGG - 1u;
-constexpr int SPIN_LIMIT = 1 << 21;
+// polls of an unpublished look-back word before the direct count is taken;
+// a negative limit never waits (every tile but the first counts directly)
+#ifndef SD_SORT_SPIN_LIMIT
+#define SD_SORT_SPIN_LIMIT (1 << 21)
+#endif
+constexpr int SPIN_LIMIT = SD_SORT_SPIN_LIMIT;
 
 // scratch words for sorting n keys in `passes` passes: per pass the
 // (tile, digit) look-back words and 256 digit totals, then one tile counter
@@ -62,7 +69,7 @@ template <typename K, typename V>
 __global__ void __launch_bounds__(THREADS) pass_kernel(const K* __restrict__ kin, const V* __restrict__ vin,
                                                        K* __restrict__ kout, V* __restrict__ vout, int n, int shift,
                                                        const uint32_t* __restrict__ totals, uint32_t* look,
-                                                       int* tile_counter, int* err, int err_bits)
+                                                       int* tile_counter)
 {
     __shared__ int s_tile;
     __shared__ uint32_t s_cnt[256];
@@ -93,25 +100,35 @@ __global__ void __launch_bounds__(THREADS) pass_kernel(const K* __restrict__ kin
     uint32_t* mine = look + (size_t)tile * 256 + tid;
     atomicExch(mine, (tile == 0 ? FLAG_PRE : FLAG_AGG) | local);
     uint32_t excl = 0;
+    bool lost = false;
     if (tile > 0) {
         int j = tile - 1;
         int spins = 0;
-        while (j >= 0) {
+        lost = SPIN_LIMIT < 0;
+        while (!lost && j >= 0) {
             uint32_t w = load_volatile(look + (size_t)j * 256 + tid);
             uint32_t f = w & ~VALUE;
             if (f == 0u) {
-                if (++spins > SPIN_LIMIT) {
-                    atomicOr(err, err_bits);
-                    break;
-                }
+                if (++spins > SPIN_LIMIT) lost = true;
                 continue;
             }
             excl += w & VALUE;
             if (f == FLAG_PRE) break;
             --j;
         }
-        atomicExch(mine, FLAG_PRE | (excl + local));
     }
+    // a wait that ran out: the prefix of digit tid over tiles 0..tile-1,
+    // counted from the keys themselves (block-uniform branch)
+    if (__syncthreads_or(lost)) {
+        run[tid] = 0;
+        __syncthreads();
+        for (int i = tid; i < base; i += THREADS) atomicAdd(&run[(unsigned)(kin[i] >> shift) & 255u], 1u);
+        __syncthreads();
+        excl = run[tid];
+        __syncthreads();
+        run[tid] = 0;
+    }
+    if (tile > 0) atomicExch(mine, FLAG_PRE | (excl + local));
     // digit base: exclusive scan of the pass's digit totals
     {
         uint32_t t = totals[tid];
@@ -159,12 +176,10 @@ __global__ void __launch_bounds__(THREADS) pass_kernel(const K* __restrict__ kin
 
 // Sorts (k0, v0) by the low `bits` bits of the key (ceil(bits / 8) passes).
 // Uses (k1, v1) as the alternate buffers; returns 0 if the result ends in
-// (k0, v0), 1 if in (k1, v1). scratch needs hist_words(n, passes) words;
-// err_bits are or-ed into the device int *err if a look-back wait ran out.
+// (k0, v0), 1 if in (k1, v1). scratch needs hist_words(n, passes) words.
 // Adds the number of kernel launches to *launches.
 template <typename K, typename V>
-int sort_pairs(K* k0, V* v0, K* k1, V* v1, int n, int bits, uint32_t* scratch, int* err, int err_bits,
-               cudaStream_t st, int* launches)
+int sort_pairs(K* k0, V* v0, K* k1, V* v1, int n, int bits, uint32_t* scratch, cudaStream_t st, int* launches)
 {
     if (n <= 1) return 0;
     const int ntiles = (n + TILE - 1) / TILE;
@@ -181,7 +196,7 @@ int sort_pairs(K* k0, V* v0, K* k1, V* v1, int n, int bits, uint32_t* scratch, i
         K* ko = cur ? k0 : k1;
         V* vo = cur ? v0 : v1;
         pass_kernel<K, V><<<ntiles, THREADS, 0, st>>>(ki, vi, ko, vo, n, 8 * p, totals + 256 * p,
-                                                      look + (size_t)p * 256 * ntiles, counters + p, err, err_bits);
+                                                      look + (size_t)p * 256 * ntiles, counters + p);
         cur ^= 1;
     }
     *launches += 1 + passes;

@@ -165,8 +165,7 @@ extern "C" int sd_sphere_trace(const sd_tree* t, const sd_trace_opts* o, float* 
                                                        depth, steps, k0, cnt);
         nl += 2;
         evals += k == 0 ? P : n;     // the first wavefront also holds the padding slots
-        int where = sdsort::sort_pairs<unsigned, int>(k0, act, k1, act1, n, 1, hist, t->status, 1 << SD_ERR_TIMEOUT,
-                                                      st, &nl);
+        int where = sdsort::sort_pairs<unsigned, int>(k0, act, k1, act1, n, 1, hist, st, &nl);
         if (where) std::swap(act, act1);
         int live = 0;
         ce = cudaMemcpyAsync(&live, cnt, sizeof(int), cudaMemcpyDeviceToHost, st);
