@@ -216,25 +216,9 @@ __device__ __forceinline__ bool bh_far(float3 q, float lx, float ly, float lz, f
     return diag2 < __fmul_rn(beta2, dbox2);
 }
 
-// Add two terms w0 2^y0 and w1 2^y1 without branches. A term that is absent
-// has w = 0 and y = SD_NEG (finite, so that differences never give NaN); the
-// running max m starts at SD_NEG as well.
+// A term that is absent has exponent SD_NEG (finite, so that differences
+// never give NaN); the running max m of a packet walk starts there as well.
 #define SD_NEG (-8.5e37f)
-template <bool GRAD>
-__device__ __forceinline__ void lse_add2(Lse& L, float y0, float w0, float3 v0, float y1, float w1, float3 v1)
-{
-    float mn = fmaxf(L.m, fmaxf(y0, y1));
-    float eo = sd_ex2(L.m - mn);
-    float c0 = w0 * sd_ex2(y0 - mn);
-    float c1 = w1 * sd_ex2(y1 - mn);
-    L.s = fmaf(L.s, eo, c0 + c1);
-    if (GRAD) {
-        L.gx = fmaf(L.gx, eo, fmaf(c0, v0.x, c1 * v1.x));
-        L.gy = fmaf(L.gy, eo, fmaf(c0, v0.y, c1 * v1.y));
-        L.gz = fmaf(L.gz, eo, fmaf(c0, v0.z, c1 * v1.z));
-    }
-    L.m = mn;
-}
 
 // merge a second LSE state (m2, s2, g2) into L
 template <bool GRAD>

@@ -156,25 +156,14 @@ __device__ __forceinline__ void queue_leaf(const SdParams& P, float3 q, int qi, 
 // offset to the box's closest point is q + max(-max(q, lo), -hi), which is
 // exactly lo - q, q - hi or 0). Accepted far fields (App. D) add
 // n_B w_B e^{-alpha d} with direction (q - y_B)/d, the mass folded into the
-// base-2 exponent y = log2(n_B w_B) - alpha log2(e) d. The LogSumExp
-// reference m is raised only when a term would exceed it by more than
-// 2^LSE_HEADROOM (a rare warp-uniform branch), and a record whose far terms
-// all lie below 2^-LSE_DROP of the reference skips their arithmetic. The
-// term that set m contributes its weight to the running sum, at least 1 for
-// a far field and at least 6e-6 (w~ clamped at 1e-6) for a leaf term; with
-// at most ~10^4 terms dropped per query the dropped mass stays below
-// 10^4 * 2^-64 / 6e-6 < 10^-10 of the sum, far under fp32 resolution.
-// Returns the lane masks of the children that must be opened and whether
-// the packet should descend into child 1 first (the child nearer to most of
-// its lanes).
-constexpr float LSE_HEADROOM = 64.f;
-constexpr float LSE_DROP = 64.f;
-
+// base-2 exponent y = log2(n_B w_B) - alpha log2(e) d, into the running
+// max-shifted LogSumExp without branches. Returns the lane masks of the
+// children that must be opened.
 template <int KINDS, bool GRAD, bool COUNT, int QK>
 __device__ __forceinline__ void packet_record(const SdParams& P, float3 q, float3 nq3, int qi, const QPrims& QP,
-                                              bool mine, unsigned mask, int rec, Lse& acc, const WarpShared& ws,
-                                              int& nq, int lane, int& ntest, int& nfar, int& nleaf, int& ref0,
-                                              int& ref1, unsigned& open0, unsigned& open1, bool& first1)
+                                              bool mine, int rec, Lse& acc, const WarpShared& ws, int& nq,
+                                              int lane, int& ntest, int& nfar, int& nleaf, int& ref0, int& ref1,
+                                              unsigned& open0, unsigned& open1)
 {
     const SdNode& r = P.nodes[rec];
     float4 a = __ldg(&r.a), b = __ldg(&r.b), c = __ldg(&r.c);
@@ -205,30 +194,23 @@ __device__ __forceinline__ void packet_record(const SdParams& P, float3 q, float
     const bool far0 = mine && __int_as_float(d.z) < rhs.x;
     const bool far1 = t1 && __int_as_float(d.w) < rhs.y;
     {
-        float r0 = rsqrtf(db.x), r1 = rsqrtf(db.y);
+        const float r0 = rsqrtf(db.x), r1 = rsqrtf(db.y);
         float2 y = __ffma2_rn(make_float2(-P.alpha2, -P.alpha2), __fmul2_rn(db, make_float2(r0, r1)), lw);
         y.x = far0 ? y.x : SD_NEG;
         y.y = far1 ? y.y : SD_NEG;
-        const float ym = fmaxf(y.x, y.y);
-        if (__any_sync(0xffffffffu, ym > acc.m + LSE_HEADROOM)) {
-            const float mn = fmaxf(acc.m, ym);
-            const float e = sd_ex2(acc.m - mn);
-            acc.s *= e;
-            if (GRAD) { acc.gx *= e; acc.gy *= e; acc.gz *= e; }
-            acc.m = mn;
+        const float mn = fmaxf(acc.m, fmaxf(y.x, y.y));
+        const float e = sd_ex2(acc.m - mn);
+        const float2 t = __fadd2_rn(y, make_float2(-mn, -mn));
+        const float c0 = far0 ? sd_ex2(t.x) : 0.f;
+        const float c1 = far1 ? sd_ex2(t.y) : 0.f;
+        acc.s = fmaf(acc.s, e, c0 + c1);
+        if (GRAD) {
+            const float2 cr = make_float2(far0 ? c0 * r0 : 0.f, far1 ? c1 * r1 : 0.f);
+            acc.gx = fmaf(acc.gx, e, fmaf(cr.x, ox.x, cr.y * ox.y));
+            acc.gy = fmaf(acc.gy, e, fmaf(cr.x, oy.x, cr.y * oy.y));
+            acc.gz = fmaf(acc.gz, e, fmaf(cr.x, oz.x, cr.y * oz.y));
         }
-        if (__any_sync(0xffffffffu, ym > acc.m - LSE_DROP)) {
-            const float2 t = __fadd2_rn(y, make_float2(-acc.m, -acc.m));
-            const float c0 = far0 ? sd_ex2(t.x) : 0.f;
-            const float c1 = far1 ? sd_ex2(t.y) : 0.f;
-            acc.s += c0 + c1;
-            if (GRAD) {
-                const float2 cr = make_float2(far0 ? c0 * r0 : 0.f, far1 ? c1 * r1 : 0.f);
-                acc.gx = fmaf(cr.x, ox.x, fmaf(cr.y, ox.y, acc.gx));
-                acc.gy = fmaf(cr.x, oy.x, fmaf(cr.y, oy.y, acc.gy));
-                acc.gz = fmaf(cr.x, oz.x, fmaf(cr.y, oz.y, acc.gz));
-            }
-        }
+        acc.m = mn;
     }
     if (COUNT) {
         ntest += mine ? (has1 ? 2 : 1) : 0;
@@ -238,8 +220,6 @@ __device__ __forceinline__ void packet_record(const SdParams& P, float3 q, float
     const bool near1 = t1 && !far1;
     const unsigned nm0 = __ballot_sync(0xffffffffu, near0);
     const unsigned nm1 = __ballot_sync(0xffffffffu, near1);
-    const unsigned p1 = __ballot_sync(0xffffffffu, mine && db.y < db.x);
-    first1 = 2 * __popc(p1) > __popc(mask);
     ref0 = d.x;
     ref1 = d.y;
     open0 = open1 = 0u;
@@ -321,24 +301,18 @@ __global__ void __launch_bounds__(PK_MAX_THREADS) k_traverse(SdParams P, const f
             const bool mine = (mask >> lane) & 1u;
             int r0, r1;
             unsigned o0, o1;
-            bool first1;
-            packet_record<KINDS, GRAD, COUNT, QK>(P, q, nq3, qi, QP, mine, mask, rec, acc, ws, nq, lane, ntest,
-                                                  nfar, nleaf, r0, r1, o0, o1, first1);
-            // descend into a child that must be opened (the nearer one when
-            // both are, so that the LogSumExp reference settles early); keep
-            // the other on the stack
+            packet_record<KINDS, GRAD, COUNT, QK>(P, q, nq3, qi, QP, mine, rec, acc, ws, nq, lane, ntest, nfar,
+                                                  nleaf, r0, r1, o0, o1);
+            // descend into a child that must be opened; keep the other on the stack
             if (o0) {
                 if (o1) {
                     if (sp < PK_STACK) {
-                        if (lane == 0) ws.stack[sp] = first1 ? make_int2(r0, (int)o0) : make_int2(r1, (int)o1);
+                        if (lane == 0) ws.stack[sp] = make_int2(r1, (int)o1);
                         ++sp;
                     } else {
                         overflow = true;
                         break;
                     }
-                    rec = first1 ? r1 : r0;
-                    mask = first1 ? o1 : o0;
-                    continue;
                 }
                 rec = r0;
                 mask = o0;
@@ -806,10 +780,11 @@ extern "C" int sd_query_status(const sd_tree* t, void* stream)
 //   * every device that loads this library holds the array until the
 //     process exits;
 //   * all calls on a device share the array and leave their contents in it,
-//     so calls that overlap on the GPU (for example on two streams) race;
+//     so calls that overlap on the GPU race, whether they are made directly
+//     (for example on two streams) or replayed from captured graphs;
 //   * the first call on a device looks up the array's device address once,
-//     with that device current; make that first call before any stream
-//     capture.
+//     with that device current, and caches it; make that first call before
+//     any stream capture. The cache does not survive cudaDeviceReset.
 // ---------------------------------------------------------------------------
 namespace {
 

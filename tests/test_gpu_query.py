@@ -79,19 +79,52 @@ def test_triangles_bh(ico4, alpha, beta, L):
     assert_parity(_np(v), _np(g), bv, bg, alpha, None, f"bh a={alpha} b={beta} L={L}")
 
 
-def test_triangles_full_size_sampled():
-    """Level-6 icosphere (81,920 triangles), all 262,144 queries in the
-    benchmark's launch configuration; 3,000 sampled outputs against the
-    oracle, plus the work counts of every sampled query."""
+@pytest.fixture(scope="module")
+def ico6():
     c = synth.config2()
-    alpha, beta = 200.0, 0.5
-    sd = _gpu(tris=(c["V"], c["F"]), alpha=alpha, beta=beta)
-    v, g, cnt = sd.query(_t(c["queries"]), counts=True)
-    idx = np.random.default_rng(0).choice(c["queries"].shape[0], 3000, replace=False)
     sc = oracle.Scene(tri_V=c["V"], tri_F=c["F"])
     sc.build_tree(1)
+    return c, sc
+
+
+@pytest.mark.parametrize("alpha", [50.0, 200.0, 1000.0])
+@pytest.mark.parametrize("beta", [0.25, 0.5, 1.0])
+def test_triangles_full_size_sampled(ico6, alpha, beta):
+    """Level-6 icosphere (81,920 triangles), all 262,144 queries of the
+    benchmark workload traversed in the benchmark's launch configuration
+    (Hilbert order from sd_query_order, persistent grid) at every (alpha,
+    beta) cell; 3,000 sampled outputs per cell against the oracle (the
+    same sample everywhere, 70 % of it in the shell), plus the work counts
+    of every sampled query."""
+    c, sc = ico6
+    sd = _gpu(tris=(c["V"], c["F"]), alpha=alpha, beta=beta)
+    q = _t(c["queries"])
+    v, g, cnt = sd.query(q, counts=True, order=sd.query_order(q))
+    idx = np.random.default_rng(0).choice(c["queries"].shape[0], 3000, replace=False)
     bv, bg, bc, _ = sc.bh(c["queries"][idx], alpha, beta)
-    assert_parity(_np(v)[idx], _np(g)[idx], bv, bg, alpha, None, "config2 sampled")
+    assert_parity(_np(v)[idx], _np(g)[idx], bv, bg, alpha, None, f"config2 sampled a={alpha} b={beta}")
+    assert np.array_equal(cnt.cpu().numpy()[idx], bc)
+    assert sd.status() == 0
+
+
+def test_street_points_full_size_sampled():
+    """Plain point queries on the street workload: the 100,002 vertices of
+    the posed body (placed in fp32 exactly as the GPU places them) against
+    2,000,000 lidar points + 50,000 wire segments, alpha 50, beta 0.5, through
+    sd_query; 3,000 sampled outputs and their work counts against the
+    oracle."""
+    from oracle import pose as PO
+    s = synth.config3_scene()
+    b = synth.config3_body()
+    X = PO.place(b["V0"], np.concatenate([b["theta"], b["p"]]), "f32")
+    sd = _gpu(points=s["points"], edges=(s["wire_V"], s["wire_E"]), alpha=50.0, beta=0.5)
+    v, g, cnt = sd.query(_t(X), counts=True)
+    assert sd.status() == 0
+    idx = np.random.default_rng(1).choice(X.shape[0], 3000, replace=False)
+    sc = oracle.Scene(points=s["points"], edge_V=s["wire_V"], edge_E=s["wire_E"])
+    sc.build_tree(1)
+    bv, bg, bc, _ = sc.bh(X[idx], 50.0, 0.5)
+    assert_parity(_np(v)[idx], _np(g)[idx], bv, bg, 50.0, None, "street sampled")
     assert np.array_equal(cnt.cpu().numpy()[idx], bc)
 
 

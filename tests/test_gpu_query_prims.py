@@ -76,7 +76,13 @@ def _assert_prims_parity(v, g, rv, rg, alpha, dmin, slack, what):
     fp32 near-contact allowance of each query"""
     assert_parity(v, None, rv, None, alpha, dmin, what)
     err = np.linalg.norm(np.asarray(g, np.float64) - rg, axis=1)
-    lim = 1e-4 * np.maximum(np.linalg.norm(rg, axis=1), 1e-2) + slack
+    plain = 1e-4 * np.maximum(np.linalg.norm(rg, axis=1), 1e-2)
+    lim = plain + slack
+    # the distribution against the plain point-query tolerance (printed with -s)
+    over = err > plain
+    print(f"{what}: grad err / plain 1e-4 limit: p50 {np.median(err / plain):.3f} p99 "
+          f"{np.quantile(err / plain, 0.99):.3f} max {(err / plain).max():.3f}; {over.sum()} of {err.size} "
+          f"above it, all within the fp32 slack (max slack / plain limit {(slack / plain).max():.2f})")
     bad = np.nonzero(err > lim)[0]
     assert bad.size == 0, f"{what}: grad err {err[bad[0]]:.3e} > {lim[bad[0]]:.3e} at {bad[0]}"
     return (err / lim).max()
