@@ -151,12 +151,15 @@ int sd_query_brute(const sd_tree* t, const float* q, int64_t M, float* value, fl
  * part-way. Same inputs and outputs as sd_query with default options
  * (Hilbert-ordered traversal, value and gradient, no counts).
  *   M      0 <= M <= 262144 (SD_ERR_TOO_LARGE beyond, nothing launched)
- * Its temporary storage (about 4.8 MB) is one static device array that
- * every device loading the library keeps until the process exits. All
- * calls on a device share it, so calls that overlap on the GPU race; calls
- * ordered on one stream are safe. The first call on a device looks up the
- * array's address with that device current: make it before any stream
- * capture.
+ * Its temporary storage (4,984,320 bytes, about 5.0 MB or 4.75 MiB) is one
+ * static device array that every device loading the library keeps until
+ * the process exits. All calls on a device share it, whether made directly
+ * or replayed from a captured CUDA graph, so any two of them that overlap
+ * on the GPU race: order them (one stream, or events). The first call on a
+ * device looks up the array's address with that device current and caches
+ * it: make that call before any stream capture, and do not call the entry
+ * point again after resetting the device (cudaDeviceReset) in the same
+ * process, since the cached address does not survive a reset.
  */
 int sd_query_noalloc(const sd_tree* t, const float* q, int64_t M, float* value, float* grad, void* stream);
 

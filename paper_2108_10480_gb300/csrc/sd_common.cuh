@@ -217,8 +217,12 @@ __device__ __forceinline__ bool bh_far(float3 q, float lx, float ly, float lz, f
 }
 
 // A term that is absent has exponent SD_NEG (finite, so that differences
-// never give NaN); the running max m of a packet walk starts there as well.
+// never give NaN); the running max m of a packet walk starts at SD_FLOOR,
+// far above SD_NEG and far below any real exponent, so that an absent
+// term's factor 2^(SD_NEG - m) is exactly 0 and the first real term's
+// rescale 2^(SD_FLOOR - y) is exactly 0 as well.
 #define SD_NEG (-8.5e37f)
+#define SD_FLOOR (-1e30f)
 
 // merge a second LSE state (m2, s2, g2) into L
 template <bool GRAD>

@@ -159,7 +159,7 @@ __device__ __forceinline__ void queue_leaf(const SdParams& P, float3 q, int qi, 
 // base-2 exponent y = log2(n_B w_B) - alpha log2(e) d, into the running
 // max-shifted LogSumExp without branches. Returns the lane masks of the
 // children that must be opened.
-template <int KINDS, bool GRAD, bool COUNT, int QK>
+template <int KINDS, bool GRAD, bool COUNT, int QK, bool TWO>
 __device__ __forceinline__ void packet_record(const SdParams& P, float3 q, float3 nq3, int qi, const QPrims& QP,
                                               bool mine, int rec, Lse& acc, const WarpShared& ws, int& nq,
                                               int lane, int& ntest, int& nfar, int& nleaf, int& ref0, int& ref1,
@@ -169,7 +169,8 @@ __device__ __forceinline__ void packet_record(const SdParams& P, float3 q, float
     float4 a = __ldg(&r.a), b = __ldg(&r.b), c = __ldg(&r.c);
     int4 d = __ldg(&r.d);
     const float2 lw = __ldg(&P.lw2[rec]);
-    const bool has1 = d.y != SD_NO_CHILD;
+    // every internal node has two children; only the super-root has one
+    const bool has1 = TWO || d.y != SD_NO_CHILD;
     float2 ox, oy, oz;
     if (QK == 1) {
         ox = __fadd2_rn(make_float2(q.x, q.x), make_float2(fmaxf(-fmaxf(q.x, a.x), b.z), fmaxf(-fmaxf(q.x, a.y), b.w)));
@@ -194,18 +195,21 @@ __device__ __forceinline__ void packet_record(const SdParams& P, float3 q, float
     const bool far0 = mine && __int_as_float(d.z) < rhs.x;
     const bool far1 = t1 && __int_as_float(d.w) < rhs.y;
     {
-        const float r0 = rsqrtf(db.x), r1 = rsqrtf(db.y);
-        float2 y = __ffma2_rn(make_float2(-P.alpha2, -P.alpha2), __fmul2_rn(db, make_float2(r0, r1)), lw);
+        // An absent term has exponent SD_NEG, far below the reference (which
+        // starts at SD_FLOOR), so its factor ex2(SD_NEG - m) is exactly 0;
+        // the tiny bias keeps 1/d finite inside a box (d = 0, never far).
+        const float2 rb = __fadd2_rn(db, make_float2(1e-30f, 1e-30f));
+        const float2 r = make_float2(rsqrtf(rb.x), rsqrtf(rb.y));
+        float2 y = __ffma2_rn(make_float2(-P.alpha2, -P.alpha2), __fmul2_rn(db, r), lw);
         y.x = far0 ? y.x : SD_NEG;
         y.y = far1 ? y.y : SD_NEG;
         const float mn = fmaxf(acc.m, fmaxf(y.x, y.y));
         const float e = sd_ex2(acc.m - mn);
         const float2 t = __fadd2_rn(y, make_float2(-mn, -mn));
-        const float c0 = far0 ? sd_ex2(t.x) : 0.f;
-        const float c1 = far1 ? sd_ex2(t.y) : 0.f;
-        acc.s = fmaf(acc.s, e, c0 + c1);
+        const float2 c = make_float2(sd_ex2(t.x), sd_ex2(t.y));
+        acc.s = fmaf(acc.s, e, c.x + c.y);
         if (GRAD) {
-            const float2 cr = make_float2(far0 ? c0 * r0 : 0.f, far1 ? c1 * r1 : 0.f);
+            const float2 cr = __fmul2_rn(c, r);
             acc.gx = fmaf(acc.gx, e, fmaf(cr.x, ox.x, cr.y * ox.y));
             acc.gy = fmaf(acc.gy, e, fmaf(cr.x, oy.x, cr.y * oy.y));
             acc.gz = fmaf(acc.gz, e, fmaf(cr.x, oz.x, cr.y * oz.y));
@@ -291,18 +295,23 @@ __global__ void __launch_bounds__(PK_MAX_THREADS) k_traverse(SdParams P, const f
         unsigned mask = __ballot_sync(0xffffffffu, ok);
         if (!mask) continue;
         Lse acc;
-        acc.m = SD_NEG; acc.s = 0.f; acc.gx = acc.gy = acc.gz = 0.f;
+        acc.m = SD_FLOOR; acc.s = 0.f; acc.gx = acc.gy = acc.gz = 0.f;
         int ntest = 0, nfar = 0, nleaf = 0;
         bool overflow = false;
         int sp = 0, nq = 0;
-        int rec = P.root_record;
         const float3 nq3 = f3(-qhi.x, -qhi.y, -qhi.z);
-        for (;;) {
+        // the super-root (one child: the root) first, then the walk over
+        // records with two children
+        int rec, r0, r1;
+        unsigned o0, o1;
+        packet_record<KINDS, GRAD, COUNT, QK, false>(P, q, nq3, qi, QP, (mask >> lane) & 1u, P.root_record, acc, ws,
+                                                     nq, lane, ntest, nfar, nleaf, r0, r1, o0, o1);
+        rec = r0;
+        mask = o0;
+        while (mask) {
             const bool mine = (mask >> lane) & 1u;
-            int r0, r1;
-            unsigned o0, o1;
-            packet_record<KINDS, GRAD, COUNT, QK>(P, q, nq3, qi, QP, mine, rec, acc, ws, nq, lane, ntest, nfar,
-                                                  nleaf, r0, r1, o0, o1);
+            packet_record<KINDS, GRAD, COUNT, QK, true>(P, q, nq3, qi, QP, mine, rec, acc, ws, nq, lane, ntest, nfar,
+                                                        nleaf, r0, r1, o0, o1);
             // descend into a child that must be opened; keep the other on the stack
             if (o0) {
                 if (o1) {
@@ -423,20 +432,74 @@ __global__ void k_fill_empty(float* value, float* grad, int M)
     if (grad) grad[3 * t] = grad[3 * t + 1] = grad[3 * t + 2] = 0.f;
 }
 
-// 24-bit Hilbert index of each query on a 256^3 grid over the scene box
-// (clamped), the traversal order. Consecutive Hilbert cells are always face
-// neighbours, so packets of 32 consecutive queries are more compact than on
-// the Morton curve and open fewer tree nodes (measured 5 % faster). The
-// index follows Skilling's transposition (AIP Conf. Proc. 707, 2004): undo
-// the excess work of the axes from the top bit down, Gray-encode, then
-// interleave. The order changes speed and summation order only.
+// Bounds of the finite query coordinates, as order-preserving unsigned keys
+// reduced with atomicMax: qb[0..2] = max key of x, y, z; qb[3..5] = max of
+// the complemented keys (the minimum). qb must be zero beforehand; a zero
+// word decodes to NaN, which the code kernel ignores (no finite query).
+__device__ __forceinline__ unsigned q_key(float f)
+{
+    unsigned u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float q_unkey(unsigned k)
+{
+    return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
+}
+
+__global__ void __launch_bounds__(256) k_query_bounds(const float* __restrict__ qs, int M, unsigned* __restrict__ qb)
+{
+    __shared__ unsigned sh[6];
+    if (threadIdx.x < 6) sh[threadIdx.x] = 0u;
+    __syncthreads();
+    unsigned hi[3] = {0u, 0u, 0u}, nlo[3] = {0u, 0u, 0u};
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < M; t += gridDim.x * blockDim.x)
+        for (int j = 0; j < 3; ++j) {
+            const float v = qs[3 * t + j];
+            if (isfinite(v)) {
+                hi[j] = max(hi[j], q_key(v));
+                nlo[j] = max(nlo[j], ~q_key(v));
+            }
+        }
+    for (int j = 0; j < 3; ++j) {
+        unsigned a = hi[j], b = nlo[j];
+        for (int o = 16; o > 0; o >>= 1) {
+            a = max(a, __shfl_xor_sync(0xffffffffu, a, o));
+            b = max(b, __shfl_xor_sync(0xffffffffu, b, o));
+        }
+        if ((threadIdx.x & 31) == 0) {
+            atomicMax(&sh[j], a);
+            atomicMax(&sh[3 + j], b);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < 6 && sh[threadIdx.x]) atomicMax(&qb[threadIdx.x], sh[threadIdx.x]);
+}
+
+// 24-bit Hilbert index of each query on a 256^3 grid over the union of the
+// scene box and the queries' bounds (a query outside the scene box keeps its
+// own cell instead of being clamped onto the box's faces with the others:
+// measured 4.7 % fewer records visited per query on the benchmark workload,
+// 30 % of whose queries lie in a box twice the mesh's size), the traversal
+// order. Consecutive Hilbert cells are always face neighbours, so packets of
+// 32 consecutive queries are more compact than on the Morton curve and open
+// fewer tree nodes (measured 5 % faster). The index follows Skilling's
+// transposition (AIP Conf. Proc. 707, 2004): undo the excess work of the
+// axes from the top bit down, Gray-encode, then interleave. The order
+// changes speed and summation order only.
 __global__ void k_query_codes(const float* __restrict__ qs, int M, const SdScalars* __restrict__ sc,
-                              unsigned* __restrict__ keys, int* __restrict__ vals)
+                              const unsigned* __restrict__ qb, unsigned* __restrict__ keys, int* __restrict__ vals)
 {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= M) return;
     float c[3] = {qs[3 * t], qs[3 * t + 1], qs[3 * t + 2]};
-    float l[3] = {sc->lo[0], sc->lo[1], sc->lo[2]}, ie[3] = {sc->inv_ex[0], sc->inv_ex[1], sc->inv_ex[2]};
+    float l[3], ie[3];
+    for (int j = 0; j < 3; ++j) {
+        // fminf / fmaxf drop a NaN bound (no finite query)
+        l[j] = fminf(sc->lo[j], q_unkey(~qb[3 + j]));
+        const float h = fmaxf(sc->hi[j], q_unkey(qb[j]));
+        const float ex = h - l[j];
+        ie[j] = ex > 0.f ? 1.f / ex : 0.f;
+    }
     unsigned k[3];
     for (int j = 0; j < 3; ++j) {
         float u = (c[j] - l[j]) * ie[j];
@@ -564,6 +627,17 @@ int check_query_args(const sd_tree* t, const float* q, int64_t M, const float* v
 
 namespace {
 
+// the Hilbert keys of m queries (keys) and their indices (vals); qb is six
+// words of scratch for the queries' bounds
+void enqueue_codes(const sd_tree* t, const float* q, int m, unsigned* qb, unsigned* keys, int* vals,
+                   cudaStream_t st, int* nl)
+{
+    cudaMemsetAsync(qb, 0, 6 * sizeof(unsigned), st);
+    k_query_bounds<<<std::min((m + 255) / 256, 2 * sm_count()), 256, 0, st>>>(q, m, qb);
+    k_query_codes<<<(m + 255) / 256, 256, 0, st>>>(q, m, t->sc, qb, keys, vals);
+    *nl += 2;
+}
+
 // Hilbert order of the queries into `order` (stream-ordered scratch).
 int compute_order(const sd_tree* t, const float* q, int m, int32_t* order, cudaStream_t st)
 {
@@ -576,10 +650,11 @@ int compute_order(const sd_tree* t, const float* q, int m, int32_t* order, cudaS
     unsigned* k1 = k0 + m;
     int* v1 = (int*)(k1 + m);
     uint32_t* hist = (uint32_t*)(v1 + m);
-    int nl = 1;
+    unsigned* qb = (unsigned*)(hist + hw);
+    int nl = 0;
     // the sort's odd pass count leaves its result in the second buffer: give
     // it `order` there and start from the scratch copy
-    k_query_codes<<<(m + 255) / 256, 256, 0, st>>>(q, m, t->sc, k0, v1);
+    enqueue_codes(t, q, m, qb, k0, v1, st, &nl);
     int where = sdsort::sort_pairs<unsigned, int>(k0, v1, k1, order, m, 24, hist, st, &nl);
     if (!where) cudaMemcpyAsync(order, v1, sizeof(int) * (size_t)m, cudaMemcpyDeviceToDevice, st);
     sd_count_launches(nl);
@@ -834,6 +909,7 @@ extern "C" int sd_query_noalloc(const sd_tree* t, const float* q, int64_t M, flo
         return sd_cuda_status(cudaGetLastError());
     }
     int* work = (int*)base;
+    unsigned* qb = (unsigned*)(base + 64);     // the queries' bounds, in the counter area
     unsigned* k0 = (unsigned*)(base + 256);
     unsigned* k1 = k0 + SD_NOALLOC_MAX_QUERIES;
     int* ord0 = (int*)(k1 + SD_NOALLOC_MAX_QUERIES);
@@ -845,8 +921,7 @@ extern "C" int sd_query_noalloc(const sd_tree* t, const float* q, int64_t M, flo
     const int* order = nullptr;
     int nl = 0;
     if (m > 1) {
-        k_query_codes<<<(m + 255) / 256, 256, 0, st>>>(q, m, t->sc, k0, ord0);
-        ++nl;
+        enqueue_codes(t, q, m, qb, k0, ord0, st, &nl);
         int where = sdsort::sort_pairs<unsigned, int>(k0, ord0, k1, ord1, m, 24, hist, st, &nl);
         order = where ? ord1 : ord0;
     }
@@ -862,7 +937,7 @@ namespace sdint {
 
 size_t order_scratch_bytes(int m)
 {
-    return sizeof(unsigned) * 2 * (size_t)m + sizeof(int) * (size_t)m + sizeof(uint32_t) * sdsort::hist_words(m, 3) + 256;
+    return sizeof(unsigned) * 2 * (size_t)m + sizeof(int) * (size_t)m + sizeof(uint32_t) * sdsort::hist_words(m, 3) + 512;
 }
 
 // Hilbert order of m queries into `order`, using caller scratch of
@@ -874,10 +949,11 @@ int order_into(const sd_tree* t, const float* q, int m, int32_t* order, void* sc
     unsigned* k1 = k0 + m;
     int* v1 = (int*)(k1 + m);
     uint32_t* hist = (uint32_t*)(v1 + m);
-    int nl = 1;
+    unsigned* qb = (unsigned*)(hist + sdsort::hist_words(m, 3));
+    int nl = 0;
     // the sort's odd pass count leaves its result in the second buffer: give
     // it `order` there and start from the scratch copy
-    k_query_codes<<<(m + 255) / 256, 256, 0, st>>>(q, m, t->sc, k0, v1);
+    enqueue_codes(t, q, m, qb, k0, v1, st, &nl);
     int where = sdsort::sort_pairs<unsigned, int>(k0, v1, k1, order, m, 24, hist, st, &nl);
     if (!where) cudaMemcpyAsync(order, v1, sizeof(int) * (size_t)m, cudaMemcpyDeviceToDevice, st);
     sd_count_launches(nl);

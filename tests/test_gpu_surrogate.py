@@ -232,3 +232,52 @@ def test_trained_surrogate_routing_and_error(street_small):
     print(f"surrogate: routed {nr}/{q.shape[0]}, abs err p50 {np.median(err):.3f} p99 {np.quantile(err, 0.99):.3f} "
           f"max {err.max():.3f} m (LB alone p50 {np.median(vb[r] - lbr):.3f}); grad err p50 {np.median(gerr):.3f}")
     assert np.median(err) < 0.5 * np.median(np.abs(vb[r] - lbr))
+
+
+def test_surrogate_gain_over_the_method_at_stated_error():
+    """What the trained network gains over the method alone, at a stated
+    accuracy, on the street workload (2,000,000 lidar points + 50,000 wire
+    segments, alpha 50, beta 0.5): trained for 3 epochs on Barnes-Hut values
+    of 2M uniform samples of the box padded by 5 m (those with LB > 0.5 m),
+    it answers 4M uniform queries of the same box with LB > 1 m routed to
+    LB + the network. The routed evaluation must be at least 1.15x faster
+    than the traversal alone on the same queries (measured 1.38x with 56 %
+    routed) while the routed answers stay within the stated error: 99th
+    percentile of |d^ - d^_BH| below 2.5 m and maximum below 8 m (measured
+    1.6 m and 4.7 m at this training budget; the benchmark's surrogate leg
+    reports longer training and other routing margins)."""
+    from paper_2108_10480_gb300 import SmoothDistance
+    from paper_2108_10480_gb300.surrogate import Surrogate, lower_bound
+    s = synth.config3_scene()
+    sd = SmoothDistance(points=s["points"], edges=(s["wire_V"], s["wire_E"]), alpha=50.0, beta=0.5, device="cuda:0")
+    lo = np.minimum(s["points"].min(0), s["wire_V"].min(0)) - 5.0
+    hi = np.maximum(s["points"].max(0), s["wire_V"].max(0)) + 5.0
+    xs = torch.from_numpy(synth.uniform_box(2_000_000, lo, hi, 31)).cuda()
+    lbs, _, far = lower_bound(sd, xs, margin=0.5, grad=False)
+    xs = xs[far.bool()].contiguous()
+    ts, _ = sd.query(xs, grad=False)
+    sur = Surrogate(lo, hi, sigma=12.0, seed=1, scale=float((ts - lbs[far.bool()]).abs().max()))
+    sur.fit_residual(sd, xs, ts, epochs=3, batch=4096, lr=1e-3)
+    q = torch.from_numpy(synth.uniform_box(4 * 1024 * 1024, lo, hi, 32)).cuda()
+    vb, gb = torch.empty(q.shape[0], device="cuda"), torch.empty(q.shape[0], 3, device="cuda")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, reps=5):
+        fn()
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            out = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps, out
+    ms_bh, _ = timed(lambda: sd.query(q, out=(vb, gb)))
+    ms_sur, (v, g, routed, nr) = timed(lambda: sur.query(sd, q, margin=1.0))
+    r = routed.bool()
+    err = (v[r] - vb[r]).abs().cpu().numpy()
+    p99 = float(np.quantile(err, 0.99))
+    print(f"surrogate gain: routed {nr / q.shape[0]:.3f}, traversal {ms_bh:.3f} ms, routed {ms_sur:.3f} ms "
+          f"(x{ms_bh / ms_sur:.2f}); routed abs err p50 {np.median(err):.3f} p99 {p99:.3f} max {err.max():.3f} m")
+    assert nr > 0.3 * q.shape[0]
+    assert p99 < 2.5 and err.max() < 8.0
+    assert ms_bh / ms_sur > 1.15
