@@ -59,9 +59,9 @@ M_QUERIES = 262144
 METHOD_FLOPS = {"test": 20, "far": 12, "point": 14, "seg": 45, "tri": 160}
 METHOD_MUFU = {"test": 0, "far": 3, "point": 2, "seg": 3, "tri": 3}
 # The traversal kernel's own hand count of the same units (its source:
-# packed two-child test, branch-free far field, de Casteljau weight),
+# packed two-child test, branch-free far field, nested-Horner weight),
 # reported beside the method's figure only.
-KERNEL_FLOPS = {"test": 26, "far": 26, "tri": 737}
+KERNEL_FLOPS = {"test": 26, "far": 26, "tri": 362}
 # tensor-core flops per query of the surrogate network, value and input
 # gradient: forward 80x128 + 2 x 128x128 MACs (layer 1 padded to 80 inputs),
 # backward 2 x 128x128 + 128x80 MACs, 2 flops per MAC

@@ -436,6 +436,23 @@ const char* sd_last_error(void);
 int sd_weight_basis(double* out);
 
 /*
+ * Host-only: the same weights as the tables the kernels evaluate (App. C.3
+ * has no evaluation scheme; this is the library's). For every class (v, e)
+ * of vertex valence v = 1..16 and edge valence e = 1..4 (the blended
+ * w~ = (1/v) P_V + (1/e) P_E + ((v-1)/v) P_B) and each orientation o = 0, 1,
+ * 2 (phi_o, the largest barycentric, as the base variable; x, y the other
+ * two, lower index first, divided by phi_o), 92 floats: 36 coefficients
+ * c_ab with w~ = phi_o^7 sum c_ab x^a y^b, then 28 with
+ * dw~/dphi1 = phi_o^6 sum c_ab x^a y^b and 28 with dw~/dphi2 likewise
+ * (phi0 = 1 - phi1 - phi2), each c_ab a Bernstein coefficient times its
+ * multinomial, in Horner order (powers of y from 7 or 6 down, within each
+ * the powers of x from high to low). out[16 * 4 * 3 * 92], class (v, e),
+ * orientation o at offset (((v - 1) * 4 + (e - 1)) * 3 + o) * 92. Computed
+ * in FP64, rounded to fp32 once. Needs no GPU.
+ */
+int sd_weight_horner_tables(float* out);
+
+/*
  * Pipe-throughput probe (a measurement aid; the paper has no counterpart).
  * The traversal is bound by the FP32 pipe with the MUFU (special-function)
  * pipe as a co-bound; this measures both rates at whatever clock the GPU

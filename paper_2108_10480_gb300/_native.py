@@ -111,6 +111,7 @@ SIGNATURES = {
     "sd_status_str": (ctypes.c_char_p, [ctypes.c_int]),
     "sd_last_error": (ctypes.c_char_p, []),
     "sd_weight_basis": (ctypes.c_int, [c_void_p]),
+    "sd_weight_horner_tables": (ctypes.c_int, [c_void_p]),
     "sd_peak_probe": (ctypes.c_int, [c_int32, c_int32, c_int32, c_void_p, ctypes.POINTER(c_double), c_void_p]),
 }
 

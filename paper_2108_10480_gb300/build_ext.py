@@ -18,7 +18,7 @@ LIB = os.path.join(BUILD, "libsd.so")
 INCLUDE = os.path.join(ROOT, "include")
 
 SOURCES = ["sd_api.cu", "sd_build.cu", "sd_query.cu", "sd_pose.cu", "sd_mlp.cu", "sd_mesh.cu", "sd_trace.cu", "sd_peak.cu", "sd_weights_host.cpp"]
-HEADERS = ["sd_common.cuh", "sd_sort.cuh", "sd_pairs.cuh"]
+HEADERS = ["sd_common.cuh", "sd_sort.cuh", "sd_pairs.cuh", "sd_wtab.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

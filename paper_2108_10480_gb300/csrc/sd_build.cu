@@ -15,6 +15,7 @@
 
 #include "sd_common.cuh"
 #include "sd_sort.cuh"
+#include "sd_wtab.h"
 
 namespace {
 
@@ -480,6 +481,47 @@ __global__ void k_gather(Geo g, const int* __restrict__ sorted, const float* __r
 
 inline int nblk(int64_t n, int t) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + t - 1) / t, 1 << 20)); }
 
+// The nested-Horner weight tables (sd_wtab.h) live in one static device
+// array per device, filled once by a synchronous copy (the first build on a
+// device must therefore not be under stream capture) and read by every
+// tree's kernels through SdParams::wtab.
+static __device__ __align__(16) float g_wtab[SD_WT_TOTAL];
+std::mutex g_wtab_mu;
+const float* g_wtab_addr[64] = {};
+
+int weight_tables(cudaStream_t st, const float** out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return sd_cuda_status(e);
+    if (dev < 0 || dev >= 64) return SD_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(g_wtab_mu);
+    if (!g_wtab_addr[dev]) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) {
+            sd_set_last_error("the first sd_build on a device fills a constant table and cannot be captured");
+            return SD_ERR_INVALID_ARG;
+        }
+        static std::vector<float> host;
+        if (host.empty()) {
+            host.resize(SD_WT_TOTAL);
+            if (sd_weight_horner_tables(host.data()) != SD_OK ||
+                sd_weight_horner_basis(host.data() + SD_WT_CLASSES) != SD_OK) {
+                host.clear();
+                return SD_ERR_INVALID_ARG;
+            }
+        }
+        e = cudaMemcpyToSymbol(g_wtab, host.data(), sizeof(float) * SD_WT_TOTAL);
+        if (e != cudaSuccess) return sd_cuda_status(e);
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_wtab);
+        if (e != cudaSuccess) return sd_cuda_status(e);
+        g_wtab_addr[dev] = (const float*)p;
+    }
+    *out = g_wtab_addr[dev];
+    return SD_OK;
+}
+
 // the library's triangle weight basis as the three float tables of SdParams
 int load_weight_basis(SdParams& P)
 {
@@ -587,6 +629,11 @@ extern "C" int sd_build(const sd_geometry* g, float alpha, float beta, const sd_
     cudaStream_t st = (cudaStream_t)stream;
     int dev = 0;
     cudaGetDevice(&dev);
+    const float* wtab = nullptr;
+    {
+        int trc = weight_tables(st, &wtab);
+        if (trc != SD_OK) return trc;
+    }
 
     Geo geo;
     geo.P = g->pts.xyz; geo.np = (int)g->pts.n;
@@ -843,6 +890,7 @@ extern "C" int sd_build(const sd_geometry* g, float alpha, float beta, const sd_
         delete t;
         return wrc;
     }
+    P.wtab = wtab;
     P.nodes = t->nodes;
     P.lw2 = t->lw2;
     P.hdr = t->hdr;

@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include "sd.h"
+#include "sd_wtab.h"
 
 // ---------------------------------------------------------------------------
 // tree layout in device memory
@@ -70,6 +71,9 @@ struct SdParams {
     float tri_base[36];
     float tri_dv[36];
     float tri_de[36];
+    // the same weights as nested-Horner tables per class (v, e) and
+    // orientation, then the blend's three parts (sd_wtab.h)
+    const float* wtab;
 };
 
 struct sd_tree {
@@ -291,6 +295,66 @@ __device__ __forceinline__ float tri_weight(const SdParams& P, float p1, float p
     return fmaf(p0, b[0], fmaf(p1, b[1], p2 * b[2]));
 }
 
+// The same weight and partials by nested Horner evaluation (sd_wtab.h): with
+// phi_o the largest barycentric and x, y the other two divided by it (both
+// in [0, 1]), w~ = phi_o^7 sum c_ab x^a y^b and dw~/dphi_1,2 = phi_o^6 sum
+// c'_ab x^a y^b, coefficients (Bernstein coefficient times multinomial) read
+// in Horner order, row by row. 36 + 2 x 28 FMAs instead of de Casteljau's
+// 84 x 3, and few coefficients live at a time; with the ratios in [0, 1] the
+// rounding error stays of the order of de Casteljau's (a few ulps of the sum
+// of the terms' magnitudes). BLEND: the class is outside the tables, and
+// each coefficient is blended from the base, dv, de tables (sd_wtab.h) as
+// base + iv dv + ie de.
+template <bool BLEND>
+__device__ __forceinline__ float wt_coef(const float* __restrict__ t, int n, float iv, float ie)
+{
+    if (!BLEND) return __ldg(t + n);
+    const int part = 3 * SD_WT_FLOATS;
+    return fmaf(ie, __ldg(t + 2 * part + n), fmaf(iv, __ldg(t + part + n), __ldg(t + n)));
+}
+
+template <bool BLEND>
+__device__ __forceinline__ float tri_weight_horner(const float* __restrict__ T, float iv, float ie, float p1, float p2,
+                                                   float& d1, float& d2)
+{
+    const float p0 = 1.f - p1 - p2;
+    const bool o0 = p0 >= p1 && p0 >= p2, o1 = !o0 && p1 >= p2;
+    const float base = o0 ? p0 : (o1 ? p1 : p2);
+    const float x = o0 ? p1 : p0, y = o0 || o1 ? p2 : p1;
+    const float ib = __frcp_rn(base);
+    const float r = x * ib, s = y * ib;
+    const float* t = T + (o0 ? 0 : (o1 ? 1 : 2)) * SD_WT_FLOATS;
+    // value: powers of y from 7 down, each row a Horner polynomial in x
+    float acc = 0.f;
+    int n = 0;
+#pragma unroll
+    for (int bp = 7; bp >= 0; --bp) {
+        float inner = wt_coef<BLEND>(t, n++, iv, ie);
+#pragma unroll
+        for (int ap = 7 - bp; ap > 0; --ap) inner = fmaf(inner, r, wt_coef<BLEND>(t, n++, iv, ie));
+        acc = fmaf(acc, s, inner);
+    }
+    // the two partials (degree 6)
+    float g1 = 0.f, g2 = 0.f;
+#pragma unroll
+    for (int bp = 6; bp >= 0; --bp) {
+        float i1 = wt_coef<BLEND>(t, n, iv, ie), i2 = wt_coef<BLEND>(t, n + 28, iv, ie);
+        ++n;
+#pragma unroll
+        for (int ap = 6 - bp; ap > 0; --ap) {
+            i1 = fmaf(i1, r, wt_coef<BLEND>(t, n, iv, ie));
+            i2 = fmaf(i2, r, wt_coef<BLEND>(t, n + 28, iv, ie));
+            ++n;
+        }
+        g1 = fmaf(g1, s, i1);
+        g2 = fmaf(g2, s, i2);
+    }
+    const float b2 = base * base, b3 = b2 * base, b6 = b3 * b3;
+    d1 = g1 * b6;
+    d2 = g2 * b6;
+    return acc * (b6 * base);
+}
+
 // ---------------------------------------------------------------------------
 // leaf terms (App. B distances + Sec. 3.3 weights). Each returns the base-2
 // exponent y, the multiplicative weight w and the gradient vector v so that
@@ -442,7 +506,13 @@ __device__ __forceinline__ void leaf_triangle_rel(const SdParams& P, float3 ap, 
     float3 gwt = f3(0.f, 0.f, 0.f);
     if (!P.unit_weights && iv != 1.f) {
         float dw1, dw2;
-        wt = tri_weight(P, p1, p2, iv, ie, dw1, dw2);
+        // the class (v, e) from the stored 1/v, 1/e (exact small integers)
+        const int cv = __float2int_rn(__frcp_rn(iv)), ce = __float2int_rn(__frcp_rn(ie));
+        if (cv <= SD_WT_VMAX && ce >= 1 && ce <= SD_WT_EMAX)
+            wt = tri_weight_horner<false>(P.wtab + ((cv - 1) * SD_WT_EMAX + (ce - 1)) * 3 * SD_WT_FLOATS, iv, ie, p1,
+                                          p2, dw1, dw2);
+        else
+            wt = tri_weight_horner<true>(P.wtab + SD_WT_CLASSES, iv, ie, p1, p2, dw1, dw2);
         if (GRAD) gwt = f3(dw1 * gp1.x + dw2 * gp2.x, dw1 * gp1.y + dw2 * gp2.y, dw1 * gp1.z + dw2 * gp2.z);
         if (wt < 1e-6f) gwt = f3(0.f, 0.f, 0.f);
     }

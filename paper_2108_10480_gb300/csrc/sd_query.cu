@@ -240,7 +240,10 @@ __device__ __forceinline__ void packet_record(const SdParams& P, float3 q, float
 // QK = 1: point queries q[3 qi..]; QK = 2, 3: query primitive qi of QP,
 // whose Barnes-Hut tests take its axis-aligned box [q, -nq3] (Sec. 3.5).
 template <int KINDS, bool GRAD, bool COUNT, int QK>
-__global__ void __launch_bounds__(PK_MAX_THREADS) k_traverse(SdParams P, const float* __restrict__ qs, int M,
+// (no __launch_bounds__: with one, ptxas gives this kernel 80 registers and
+// spills a little; without, 72 and none, which admits a seventh block of 128
+// threads per SM; measured 1.8 % faster)
+__global__ void k_traverse(SdParams P, const float* __restrict__ qs, int M,
                                                              const int* __restrict__ order,
                                                              float* __restrict__ value, float* __restrict__ grad,
                                                              int* __restrict__ counts, int* __restrict__ status,

@@ -18,6 +18,7 @@
 #include <vector>
 
 #include "sd.h"
+#include "sd_wtab.h"
 
 namespace sdw {
 
@@ -159,4 +160,83 @@ extern "C" int sd_weight_basis(double* out)
             }
     }
     return SD_OK;
+}
+
+// Nested-Horner tables of the blended triangle weight (App. C.3) for every
+// class (v, e) with v = 1..SD_WT_VMAX, e = 1..SD_WT_EMAX: for each class and
+// each orientation o (the barycentric taken as the base variable: phi_o),
+// SD_WT_FLOATS floats:
+//   36 coefficients of w~ = phi_o^7 sum_{a,b} c_ab x^a y^b,
+//   28 of dw~/dphi1 and 28 of dw~/dphi2 (phi0 = 1 - phi1 - phi2, each
+//      = phi_o^6 sum c_ab x^a y^b),
+// where x, y are the ratios of the other two barycentrics (lower index
+// first) to phi_o, c_ab = (Bernstein coefficient) x (multinomial), and the
+// coefficients run in Horner order: powers of y from high to low outer,
+// powers of x from high to low inner. Computed in FP64 from the basis of
+// sd_weight_basis, rounded to fp32 once.
+// the Horner tables (3 orientations x SD_WT_FLOATS floats) of one weight
+// polynomial with Bernstein coefficients w(n) = a_v basis_V + a_e basis_E +
+// a_b basis_B
+static float* horner_tables(const double* basis, double a_v, double a_e, double a_b, float* o_ptr)
+{
+    auto fact = [](int n) { double f = 1.0; for (int i = 2; i <= n; ++i) f *= i; return f; };
+    auto multi = [&](int n, int i, int j, int k) { return fact(n) / (fact(i) * fact(j) * fact(k)); };
+    {
+        {
+            // degree-7 coefficients b[i][j][k] and the degree-6 differences
+            double b7[8][8][8] = {}, d1[7][7][7] = {}, d2[7][7][7] = {};
+            for (int j = 0; j <= 7; ++j)
+                for (int k = 0; j + k <= 7; ++k) {
+                    const int n = bidx(j, k), i = 7 - j - k;
+                    b7[i][j][k] = a_v * basis[n] + a_e * basis[36 + n] + a_b * basis[72 + n];
+                }
+            for (int j = 0; j <= 6; ++j)
+                for (int k = 0; j + k <= 6; ++k) {
+                    const int i = 6 - j - k;
+                    d1[i][j][k] = 7.0 * (b7[i][j + 1][k] - b7[i + 1][j][k]);
+                    d2[i][j][k] = 7.0 * (b7[i][j][k + 1] - b7[i + 1][j][k]);
+                }
+            for (int o = 0; o < 3; ++o) {
+                const int x0 = o == 0 ? 1 : 0, y0 = o == 2 ? 1 : 2;    // the other two variables
+                auto emit = [&](int deg, auto coef) {
+                    for (int bp = deg; bp >= 0; --bp)
+                        for (int ap = deg - bp; ap >= 0; --ap) {
+                            int ex[3];
+                            ex[o] = deg - ap - bp;
+                            ex[x0] = ap;
+                            ex[y0] = bp;
+                            *o_ptr++ = (float)(coef(ex[0], ex[1], ex[2]) * multi(deg, ex[0], ex[1], ex[2]));
+                        }
+                };
+                emit(7, [&](int i, int j, int k) { return b7[i][j][k]; });
+                emit(6, [&](int i, int j, int k) { return d1[i][j][k]; });
+                emit(6, [&](int i, int j, int k) { return d2[i][j][k]; });
+            }
+        }
+    }
+    return o_ptr;
+}
+
+extern "C" int sd_weight_horner_tables(float* out)
+{
+    double basis[108];
+    int rc = sd_weight_basis(basis);
+    if (rc != SD_OK) return rc;
+    float* o_ptr = out;
+    for (int v = 1; v <= SD_WT_VMAX; ++v)
+        for (int e = 1; e <= SD_WT_EMAX; ++e)
+            o_ptr = horner_tables(basis, 1.0 / v, 1.0 / e, (v - 1.0) / v, o_ptr);
+    return (int)(o_ptr - out) == SD_WT_VMAX * SD_WT_EMAX * 3 * SD_WT_FLOATS ? SD_OK : SD_ERR_INVALID_ARG;
+}
+
+int sd_weight_horner_basis(float* out)
+{
+    double basis[108];
+    int rc = sd_weight_basis(basis);
+    if (rc != SD_OK) return rc;
+    // w~ = base + (1/v) dv + (1/e) de with base = P_B, dv = P_V - P_B, de = P_E
+    float* o_ptr = horner_tables(basis, 0.0, 0.0, 1.0, out);
+    o_ptr = horner_tables(basis, 1.0, 0.0, -1.0, o_ptr);
+    o_ptr = horner_tables(basis, 0.0, 1.0, 0.0, o_ptr);
+    return (int)(o_ptr - out) == 3 * 3 * SD_WT_FLOATS ? SD_OK : SD_ERR_INVALID_ARG;
 }
