@@ -281,3 +281,27 @@ def test_surrogate_gain_over_the_method_at_stated_error():
     assert nr > 0.3 * q.shape[0]
     assert p99 < 2.5 and err.max() < 8.0
     assert ms_bh / ms_sur > 1.15
+
+
+def test_lower_bound_is_certified_at_alpha_1000_on_the_street():
+    """The certified bound at the sharpest alpha of the workloads, on the
+    street (2,000,000 points + 50,000 wire segments, coordinates up to
+    420 m): at 512 queries spread over the box padded by 5 m, the GPU's LB
+    (fp32, lowered by its 1e-3 + 1e-5 |LB| allowance) stays at or below the
+    FP64 oracle's exact d^ (brute force over every primitive). The
+    allowance covers the fp32 rounding bound
+    6 u (|q|_inf + d_max) + 70 u / alpha + u |LB| (u = 2^-24), about 2e-4 m
+    here."""
+    from paper_2108_10480_gb300 import SmoothDistance
+    from paper_2108_10480_gb300.surrogate import lower_bound
+    s = synth.config3_scene()
+    sd = SmoothDistance(points=s["points"], edges=(s["wire_V"], s["wire_E"]), alpha=1000.0, beta=0.5,
+                        device="cuda:0")
+    lo = np.minimum(s["points"].min(0), s["wire_V"].min(0)) - 5.0
+    hi = np.maximum(s["points"].max(0), s["wire_V"].max(0)) + 5.0
+    q = synth.uniform_box(512, lo, hi, 41)
+    lb, _, _ = lower_bound(sd, torch.from_numpy(q).cuda(), margin=0.0, grad=False)
+    lb = lb.cpu().numpy().astype(np.float64)
+    exact, _, _ = oracle.Scene(points=s["points"], edge_V=s["wire_V"], edge_E=s["wire_E"]).brute(q, 1000.0)
+    assert np.all(lb <= exact), (lb - exact).max()
+    assert np.median(exact - lb) < 20.0     # a bound, not a vacuous one
