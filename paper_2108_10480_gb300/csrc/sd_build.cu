@@ -127,7 +127,6 @@ struct InitJob {
     int* status;
     float* params; int nparams;
     int4* nodes; int nnodes4;
-    int* visits; int nvisits;
     int* ecnt; int nev;
     int* vcnt; int ntv;
     int* hcnt; unsigned long long* hkeys; int hcap;
@@ -147,7 +146,6 @@ __global__ void k_init(InitJob J)
     }
     for (int i = t0; i < J.nparams; i += st) J.params[i] = 0.f;
     for (int i = t0; i < J.nnodes4; i += st) J.nodes[i] = make_int4(0, 0, 0, 0);
-    for (int i = t0; i < J.nvisits; i += st) J.visits[i] = 0;
     for (int i = t0; i < J.nev; i += st) J.ecnt[i] = 0;
     for (int i = t0; i < J.ntv; i += st) J.vcnt[i] = 0;
     for (int i = t0; i < J.hcap; i += st) { J.hcnt[i] = 0; J.hkeys[i] = ~0ull; }
@@ -284,7 +282,7 @@ __device__ __forceinline__ int bucket_prefix(const unsigned long long* sk, const
 
 __global__ void k_karras(const unsigned long long* __restrict__ sk, const int* __restrict__ sv, int L, int nb,
                          int* __restrict__ left, int* __restrict__ right, int* __restrict__ parent_int,
-                         int* __restrict__ parent_leaf, SdNode* __restrict__ nodes)
+                         int2* __restrict__ range, SdNode* __restrict__ nodes)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nb - 1) return;
@@ -310,8 +308,9 @@ __global__ void k_karras(const unsigned long long* __restrict__ sk, const int* _
     int rref = (hi == gamma + 1) ? -(gamma + 2) : gamma + 1;
     left[i] = lref;
     right[i] = rref;
-    if (lref < 0) parent_leaf[gamma] = i; else parent_int[gamma] = i;
-    if (rref < 0) parent_leaf[gamma + 1] = i; else parent_int[gamma + 1] = i;
+    range[i] = make_int2(lo, hi);
+    if (lref >= 0) parent_int[gamma] = i;
+    if (rref >= 0) parent_int[gamma + 1] = i;
     nodes[i].d.x = lref;
     nodes[i].d.y = rref;
     if (i == 0) parent_int[0] = -1;
@@ -334,84 +333,158 @@ __device__ __forceinline__ void write_slot(SdNode* nodes, float2* lw2, int rec, 
     w[slot] = log2f(nw);
 }
 
-// Bottom-up aggregates: a thread per bucket computes the bucket's AABB over
-// all its primitive vertices (exact fp32 min/max), its count and whether it
-// holds only points, then climbs; the second child to arrive at a node
-// merges both children and continues (no thread ever waits).
-__global__ void k_aggregate(Geo g, const int* __restrict__ sorted, int L, int nb, const int* __restrict__ left,
-                            const int* __restrict__ right, const int* __restrict__ parent_int,
-                            const int* __restrict__ parent_leaf, float* node_box, int* node_count, int* node_pts,
-                            float* leaf_box, int* leaf_count, int* leaf_pts, int* visits, SdNode* nodes,
-                            float2* lw2, const BuildScalars* bs, float S, int unit)
+// Aggregates without a bottom-up climb. Every node of the radix tree covers a
+// contiguous range of buckets, so its AABB (an exact fp32 min/max, the same
+// in any order of reduction), its primitive count and whether it holds only
+// points are reductions over that range. k_leaves computes every bucket's
+// own aggregates and, in each block of 1,024 buckets, the unions over every
+// aligned run of 2^k buckets (k = 0..10); k_nodes then assembles each
+// internal node from at most 2 x 10 aligned runs plus whole runs of 1,024,
+// loaded independently of one another. A run entry is two float4:
+// (lo.x, lo.y, lo.z, 1 if points only else 0) and (hi.x, hi.y, hi.z, 0).
+constexpr int AGG_T = 1024;
+constexpr int AGG_LEVELS = 11;
+
+// first entry of level k of the run table (levels 0..k-1 before it)
+__host__ __device__ __forceinline__ int64_t run_level_offset(int nb, int k)
 {
-    int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= nb) return;
-    float wfar = 1.f;
-    if (!unit) {
-        float A = (float)max(max(bs->A_E, bs->A_T), 1);
-        wfar = (S == 1.f) ? A : powf(A, S);
-    }
+    int64_t off = 0;
+    for (int j = 0; j < k; ++j) off += (nb + (1 << j) - 1) >> j;
+    return off;
+}
+
+__device__ __forceinline__ float far_weight(const BuildScalars* bs, float S, int unit)
+{
+    if (unit) return 1.f;
+    float A = (float)max(max(bs->A_E, bs->A_T), 1);
+    return (S == 1.f) ? A : powf(A, S);
+}
+
+__global__ void __launch_bounds__(AGG_T) k_leaves(Geo g, const int* __restrict__ sorted, int L, int nb,
+                                                  float* __restrict__ leaf_box, int* __restrict__ leaf_count,
+                                                  float4* __restrict__ runs, SdNode* nodes, float2* lw2,
+                                                  const BuildScalars* bs, float S, int unit)
+{
+    __shared__ float s_lo[3][AGG_T], s_hi[3][AGG_T];
+    __shared__ int s_pts[AGG_T];
+    const int t = threadIdx.x;
+    const int b = blockIdx.x * AGG_T + t;
     float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
-    int k0 = b * L, k1 = min(k0 + L, g.n);
     int pts = 1;
-    for (int k = k0; k < k1; ++k) {
-        int p = sorted[k];
-        int nvx = prim_nv(g, p);
-        if (nvx > 1) pts = 0;
-        for (int j = 0; j < nvx; ++j) {
-            float3 v = prim_vertex(g, p, j);
-            lo[0] = fminf(lo[0], v.x); lo[1] = fminf(lo[1], v.y); lo[2] = fminf(lo[2], v.z);
-            hi[0] = fmaxf(hi[0], v.x); hi[1] = fmaxf(hi[1], v.y); hi[2] = fmaxf(hi[2], v.z);
+    if (b < nb) {
+        const int k0 = b * L, k1 = min(k0 + L, g.n);
+        for (int k = k0; k < k1; ++k) {
+            const int p = sorted[k];
+            const int nvx = prim_nv(g, p);
+            if (nvx > 1) pts = 0;
+            for (int j = 0; j < nvx; ++j) {
+                const float3 v = prim_vertex(g, p, j);
+                lo[0] = fminf(lo[0], v.x); lo[1] = fminf(lo[1], v.y); lo[2] = fminf(lo[2], v.z);
+                hi[0] = fmaxf(hi[0], v.x); hi[1] = fmaxf(hi[1], v.y); hi[2] = fmaxf(hi[2], v.z);
+            }
+        }
+        for (int j = 0; j < 3; ++j) { leaf_box[6 * b + j] = lo[j]; leaf_box[6 * b + 3 + j] = hi[j]; }
+        leaf_count[b] = k1 - k0;
+        runs[2 * (int64_t)b] = make_float4(lo[0], lo[1], lo[2], (float)pts);
+        runs[2 * (int64_t)b + 1] = make_float4(hi[0], hi[1], hi[2], 0.f);
+        if (nb == 1) {
+            // the only bucket is the root: the super-root's one child
+            const float nw = pts ? (float)(k1 - k0) : __fmul_rn((float)(k1 - k0), far_weight(bs, S, unit));
+            write_slot(nodes, lw2, nb - 1, 0, lo, hi, nw);
         }
     }
-    int count = k1 - k0;
-    for (int j = 0; j < 3; ++j) { leaf_box[6 * b + j] = lo[j]; leaf_box[6 * b + 3 + j] = hi[j]; }
-    leaf_count[b] = count;
-    leaf_pts[b] = pts;
-    float nw = pts ? (float)count : __fmul_rn((float)count, wfar);
-    int par = nb > 1 ? parent_leaf[b] : -1;
-    if (par < 0) { write_slot(nodes, lw2, nb - 1, 0, lo, hi, nw); return; }
-    int from = -(b + 1);        // the child this thread arrives from
-    int lr = __ldg(&left[par]), rr = __ldg(&right[par]);
-    write_slot(nodes, lw2, par, lr == from ? 0 : 1, lo, hi, nw);
-    int node = par;
-    // Up the tree: the second thread to reach a node merges its own child's
-    // aggregates (still in registers) with the sibling's, which the first
-    // thread published before its increment. The topology arrays are
-    // read-only here, so the next level's references are fetched early.
-    while (node >= 0) {
-        const int pp = __ldg(&parent_int[node]);
-        const int plr = pp >= 0 ? __ldg(&left[pp]) : 0, prr = pp >= 0 ? __ldg(&right[pp]) : 0;
-        __threadfence();
-        if (atomicAdd(&visits[node], 1) == 0) return;
-        __threadfence();
-        const int sib = lr == from ? rr : lr;
-        const float* bx;
-        int cc, cp;
-        if (sib < 0) {
-            const int lb = -sib - 1;
-            bx = leaf_box + 6 * lb;
-            cc = __ldcg(&leaf_count[lb]); cp = __ldcg(&leaf_pts[lb]);
-        } else {
-            bx = node_box + 6 * sib;
-            cc = __ldcg(&node_count[sib]); cp = __ldcg(&node_pts[sib]);
+    for (int j = 0; j < 3; ++j) { s_lo[j][t] = lo[j]; s_hi[j][t] = hi[j]; }
+    s_pts[t] = pts;
+    for (int k = 1; k < AGG_LEVELS; ++k) {
+        __syncthreads();
+        if (t < (AGG_T >> k)) {
+            const int i0 = t << k, i1 = i0 + (1 << (k - 1));
+            float a[3], c[3];
+            for (int j = 0; j < 3; ++j) {
+                a[j] = fminf(s_lo[j][i0], s_lo[j][i1]);
+                c[j] = fmaxf(s_hi[j][i0], s_hi[j][i1]);
+                s_lo[j][i0] = a[j];
+                s_hi[j][i0] = c[j];
+            }
+            const int f = s_pts[i0] & s_pts[i1];
+            s_pts[i0] = f;
+            const int64_t r = (int64_t)blockIdx.x * (AGG_T >> k) + t;       // run index at level k
+            if ((r << k) < nb) {
+                const int64_t e = run_level_offset(nb, k) + r;
+                runs[2 * e] = make_float4(a[0], a[1], a[2], (float)f);
+                runs[2 * e + 1] = make_float4(c[0], c[1], c[2], 0.f);
+            }
         }
-        for (int j = 0; j < 3; ++j) {
-            lo[j] = fminf(lo[j], __ldcg(&bx[j]));
-            hi[j] = fmaxf(hi[j], __ldcg(&bx[3 + j]));
+    }
+}
+
+// one thread per internal node: its aggregates, its slot in its parent's
+// record (the super-root's for the root) and the slots of its leaf children
+__global__ void k_nodes(int nb, int L, int n, const int2* __restrict__ range, const int* __restrict__ left,
+                        const int* __restrict__ right, const int* __restrict__ parent_int,
+                        const float4* __restrict__ runs, float* __restrict__ node_box, int* __restrict__ node_count,
+                        SdNode* nodes, float2* lw2, const BuildScalars* bs, float S, int unit)
+{
+    __shared__ int64_t s_off[AGG_LEVELS];
+    if (threadIdx.x < AGG_LEVELS) s_off[threadIdx.x] = run_level_offset(nb, threadIdx.x);
+    __syncthreads();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nb - 1) return;
+    const float wfar = far_weight(bs, S, unit);
+    const int2 rg = __ldg(&range[i]);
+    const int a = rg.x, e = rg.y + 1;       // buckets [a, e)
+    float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    float pts = 1.f;
+    int x = a;
+    while (x < e) {
+        // the next eight aligned runs in [x, e), largest first at each step
+        int64_t ent[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            ent[q] = -1;
+            if (x < e) {
+                int k = x ? __ffs(x) - 1 : AGG_LEVELS - 1;
+                k = min(min(k, AGG_LEVELS - 1), 31 - __clz(e - x));
+                ent[q] = s_off[k] + (x >> k);
+                x += 1 << k;
+            }
         }
-        count += cc;
-        pts &= cp;
-        for (int j = 0; j < 3; ++j) { node_box[6 * node + j] = lo[j]; node_box[6 * node + 3 + j] = hi[j]; }
-        node_count[node] = count;
-        node_pts[node] = pts;
-        const float nnw = pts ? (float)count : __fmul_rn((float)count, wfar);
-        if (pp < 0) { write_slot(nodes, lw2, nb - 1, 0, lo, hi, nnw); return; }
-        write_slot(nodes, lw2, pp, plr == node ? 0 : 1, lo, hi, nnw);
-        from = node;
-        lr = plr;
-        rr = prr;
-        node = pp;
+        float4 A[8], B[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            if (ent[q] >= 0) {
+                A[q] = __ldg(&runs[2 * ent[q]]);
+                B[q] = __ldg(&runs[2 * ent[q] + 1]);
+            } else {
+                A[q] = make_float4(INFINITY, INFINITY, INFINITY, 1.f);
+                B[q] = make_float4(-INFINITY, -INFINITY, -INFINITY, 0.f);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            lo[0] = fminf(lo[0], A[q].x); lo[1] = fminf(lo[1], A[q].y); lo[2] = fminf(lo[2], A[q].z);
+            hi[0] = fmaxf(hi[0], B[q].x); hi[1] = fmaxf(hi[1], B[q].y); hi[2] = fmaxf(hi[2], B[q].z);
+            pts = fminf(pts, A[q].w);
+        }
+    }
+    const int count = min((int64_t)e * L, (int64_t)n) - a * L;
+    for (int j = 0; j < 3; ++j) { node_box[6 * i + j] = lo[j]; node_box[6 * i + 3 + j] = hi[j]; }
+    node_count[i] = count;
+    const float nw = pts != 0.f ? (float)count : __fmul_rn((float)count, wfar);
+    const int p = __ldg(&parent_int[i]);
+    if (p < 0) write_slot(nodes, lw2, nb - 1, 0, lo, hi, nw);
+    else write_slot(nodes, lw2, p, __ldg(&left[p]) == i ? 0 : 1, lo, hi, nw);
+    // leaf children
+    const int ch[2] = {__ldg(&left[i]), __ldg(&right[i])};
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        if (ch[c] >= 0) continue;
+        const int lb = -ch[c] - 1;
+        const float4 la = __ldg(&runs[2 * (int64_t)lb]), lh = __ldg(&runs[2 * (int64_t)lb + 1]);
+        const float llo[3] = {la.x, la.y, la.z}, lhi[3] = {lh.x, lh.y, lh.z};
+        const int lc = min((lb + 1) * L, n) - lb * L;
+        const float lw = la.w != 0.f ? (float)lc : __fmul_rn((float)lc, wfar);
+        write_slot(nodes, lw2, i, c, llo, lhi, lw);
     }
 }
 
@@ -708,10 +781,8 @@ extern "C" int sd_build(const sd_geometry* g, float alpha, float beta, const sd_
     size_t t_hkeys = tcarve(geo.nf ? sizeof(unsigned long long) * hcap : 8);
     size_t t_hcnt = tcarve(geo.nf ? sizeof(int) * hcap : 4);
     size_t t_pint = tcarve(sizeof(int) * std::max(nb, 1));
-    size_t t_pleaf = tcarve(sizeof(int) * std::max(nb, 1));
-    size_t t_visits = tcarve(sizeof(int) * std::max(nb, 1));
-    size_t t_npts = tcarve(sizeof(int) * std::max(nb, 1));
-    size_t t_lpts = tcarve(sizeof(int) * std::max(nb, 1));
+    size_t t_range = tcarve(sizeof(int2) * std::max(nb, 1));
+    size_t t_runs = tcarve(2 * sizeof(float4) * (size_t)std::max<int64_t>(run_level_offset(nb, AGG_LEVELS), 1));
     void* tmp = nullptr;
     ce = cudaMallocAsync(&tmp, toff, st);
     if (ce != cudaSuccess) { cudaFreeAsync(t->mem, st); delete t; cudaGetLastError(); return SD_ERR_OOM; }
@@ -727,10 +798,8 @@ extern "C" int sd_build(const sd_geometry* g, float alpha, float beta, const sd_
     auto* hkeys = (unsigned long long*)(tb + t_hkeys);
     int* hcnt = (int*)(tb + t_hcnt);
     int* pint = (int*)(tb + t_pint);
-    int* pleaf = (int*)(tb + t_pleaf);
-    int* visits = (int*)(tb + t_visits);
-    int* npts = (int*)(tb + t_npts);
-    int* lpts = (int*)(tb + t_lpts);
+    int2* range = (int2*)(tb + t_range);
+    float4* runs = (float4*)(tb + t_runs);
 
     const int T = 256;
     int nl = 0;   // kernel launches of this build
@@ -739,11 +808,10 @@ extern "C" int sd_build(const sd_geometry* g, float alpha, float beta, const sd_
         J.bs = bs; J.status = t->status;
         J.params = t->params; J.nparams = 2 * std::max(n, 1);
         J.nodes = (int4*)t->nodes; J.nnodes4 = 4 * std::max(nb, 1);
-        J.visits = visits; J.nvisits = std::max(nb, 1);
         J.ecnt = ecnt; J.nev = geo.ne ? geo.nev : 0;
         J.vcnt = vcnt; J.ntv = geo.nf ? geo.ntv : 0;
         J.hcnt = hcnt; J.hkeys = hkeys; J.hcap = geo.nf ? (int)hcap : 0;
-        int work = std::max({J.nparams, J.nnodes4, J.nvisits, J.nev, J.ntv, J.hcap});
+        int work = std::max({J.nparams, J.nnodes4, J.nev, J.ntv, J.hcap});
         ++nl;
         k_init<<<std::min(nblk(work, T), 1024), T, 0, st>>>(J);
     }
@@ -772,15 +840,16 @@ extern "C" int sd_build(const sd_geometry* g, float alpha, float beta, const sd_
 
     // The weight parameters (incidence counts, App. C.2-C.3) do not feed the
     // Morton codes, the sort or the topology: they run on the side stream
-    // from here on, and the leaf-order gather follows them there once the
-    // sort is done; the aggregates (which need A) and the end of the build
-    // wait for them. Without a side stream everything stays on `st`.
+    // from here on, and the leaf-order gather and the bucket aggregates
+    // follow them there once the sort is done, beside the topology; the
+    // internal nodes' aggregates (which need A and the topology) and the end
+    // of the build wait for them. Without a side stream everything stays on
+    // `st`.
     cudaStream_t ps = st;
-    cudaEvent_t ev_fork = nullptr, ev_params = nullptr, ev_sorted = nullptr, ev_gather = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_sorted = nullptr, ev_gather = nullptr;
     if (n > 0 && (geo.ne || geo.nf)) {
         cudaStream_t sd = side_stream(dev);
         if (sd && cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming) == cudaSuccess &&
-            cudaEventCreateWithFlags(&ev_params, cudaEventDisableTiming) == cudaSuccess &&
             cudaEventCreateWithFlags(&ev_sorted, cudaEventDisableTiming) == cudaSuccess &&
             cudaEventCreateWithFlags(&ev_gather, cudaEventDisableTiming) == cudaSuccess &&
             cudaEventRecord(ev_fork, st) == cudaSuccess && cudaStreamWaitEvent(sd, ev_fork, 0) == cudaSuccess) {
@@ -805,7 +874,6 @@ extern "C" int sd_build(const sd_geometry* g, float alpha, float beta, const sd_
         k_tri_params<<<nblk(geo.nf, T), T, 0, ps>>>(geo.F, geo.nf, geo.ntv, vcnt, hkeys, hcnt, hcap - 1, t->params,
                                                      geo.np + geo.ne, bs);
     }
-    if (ps != st) cudaEventRecord(ev_params, ps);
     if (n > 0) {
         // Morton order
         ++nl;
@@ -820,24 +888,27 @@ extern "C" int sd_build(const sd_geometry* g, float alpha, float beta, const sd_
         }
         ++nl;
         k_gather<<<nblk(n, T), T, 0, ps>>>(geo, sv, t->params, t->hdr, t->ext, t->sorted);
+        // every bucket's aggregates and their aligned runs, beside the topology
+        ++nl;
+        k_leaves<<<nblk(nb, AGG_T), AGG_T, 0, ps>>>(geo, sv, L, nb, t->leaf_box, t->leaf_count, runs, t->nodes, t->lw2,
+                                                     bs, S, t->weights_unit);
         if (ps != st) cudaEventRecord(ev_gather, ps);
         // topology
         if (nb > 1) {
             ++nl;
-            k_karras<<<nblk(nb - 1, T), T, 0, st>>>(sk, sv, L, nb, t->left, t->right, pint, pleaf, t->nodes);
+            k_karras<<<nblk(nb - 1, T), T, 0, st>>>(sk, sv, L, nb, t->left, t->right, pint, range, t->nodes);
         }
         ++nl;
         k_super_root<<<1, 1, 0, st>>>(t->nodes, t->lw2, nb);
-        // aggregates (far-field weights use A)
-        if (ps != st) cudaStreamWaitEvent(st, ev_params, 0);
-        ++nl;
-        k_aggregate<<<nblk(nb, T), T, 0, st>>>(geo, sv, L, nb, t->left, t->right, pint, pleaf, t->node_box,
-                                                t->node_count,
-                                                npts, t->leaf_box, t->leaf_count, lpts, visits, t->nodes, t->lw2,
-                                                bs, S, t->weights_unit);
+        // internal nodes from the runs (far-field weights use A)
         if (ps != st) cudaStreamWaitEvent(st, ev_gather, 0);
+        if (nb > 1) {
+            ++nl;
+            k_nodes<<<nblk(nb - 1, T), T, 0, st>>>(nb, L, n, range, t->left, t->right, pint, runs, t->node_box,
+                                                   t->node_count, t->nodes, t->lw2, bs, S, t->weights_unit);
+        }
     }
-    for (cudaEvent_t e : {ev_fork, ev_params, ev_sorted, ev_gather})
+    for (cudaEvent_t e : {ev_fork, ev_sorted, ev_gather})
         if (e) cudaEventDestroy(e);
     ++nl;
     k_finalize<<<1, 32, 0, st>>>(bs, t->weights_unit, t->sc, t->status);

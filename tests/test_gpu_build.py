@@ -33,13 +33,18 @@ def _scene(name):
         P = synth.points_on_sphere(500, 0.02, 3) * 1.4
         return (dict(points=P, edges=(Ve, E), tris=(V, F)),
                 oracle.Scene(points=P, edge_V=Ve, edge_E=E, tri_V=V, tri_F=F))
+    if name in ("points_cap", "points_cap1"):
+        # 131,072 primitives fill 128 sort tiles of 1,024 keys exactly; one
+        # more adds a tile that holds a single key
+        P = synth.points_on_sphere(131_072 + (name == "points_cap1"), 0.005, 5)
+        return dict(points=P), oracle.Scene(points=P)
     if name == "ico6":
         c = synth.config2(m=16)
         return dict(tris=(c["V"], c["F"])), oracle.Scene(tri_V=c["V"], tri_F=c["F"])
     raise KeyError(name)
 
 
-@pytest.mark.parametrize("name", ["points", "dup_points", "tris", "mixed", "ico6"])
+@pytest.mark.parametrize("name", ["points", "dup_points", "tris", "mixed", "ico6", "points_cap", "points_cap1"])
 @pytest.mark.parametrize("L", [1, 4, 7])
 def test_build_bit_exact(name, L):
     kw, sc = _scene(name)

@@ -1,6 +1,7 @@
 """GPU sphere tracing (sd_sphere_trace) against the oracle's tracer on a
 small bumpy mesh as points, edges and triangles, exact and Barnes-Hut:
-the same rays hit, at the same depth up to the march's resolution."""
+the same rays hit (every ray whose marches both end within the step
+budget), at the same depth up to the march's resolution."""
 import numpy as np
 import pytest
 import torch
@@ -38,7 +39,12 @@ def test_trace_matches_oracle(kind, beta):
     rd, rs = OT.sphere_trace(sc, cam, 200.0, beta, alpha_u=1200.0, eps=EPS, t_max=t_max, max_steps=256)
     hg, hr = np.isfinite(depth), np.isfinite(rd)
     assert hr.sum() > 200 and (~hr).sum() > 200            # the object and the background both in view
-    assert (hg != hr).mean() <= 0.02, f"{kind} beta={beta}: hit masks differ on {(hg != hr).sum()} rays"
+    # A ray's hit decision may differ only where one of the two marches ran
+    # out of steps (a grazing ray still closing in on the surface, where
+    # fp32 and fp64 steps part ways); everywhere else both must agree.
+    gs = steps.cpu().numpy().ravel()
+    differ = (hg != hr) & (gs < 256) & (rs < 256)
+    assert not differ.any(), f"{kind} beta={beta}: hit masks differ on {differ.sum()} rays"
     both = hg & hr
     err = np.abs(depth[both] - rd[both])
     assert np.all(err <= 4 * EPS + 1e-5 * rd[both]), f"{kind} beta={beta}: depth err {err.max():.3e}"
