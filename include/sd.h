@@ -99,9 +99,9 @@ void sd_default_query_opts(sd_query_opts* o);
  * opts->defer_checks = 1 it returns after enqueueing the build: the same
  * kernels run (indices are clamped where they are dereferenced, so bad input
  * cannot fault) and their verdict is reported by sd_query_status.
- * The weight parameters and the leaf-order gather run on a library-owned
- * side stream of the device, joined back into `stream` by events before
- * the build ends; builds on several streams of one device share that side
+ * The weight parameters run on a library-owned side stream of the device,
+ * joined back into `stream` by an event after the sort; builds on several
+ * streams of one device share that side
  * stream (their parameter phases queue behind one another), and a build
  * enqueued under stream capture takes the side stream into the capture, so
  * no other build may run on the device meanwhile.

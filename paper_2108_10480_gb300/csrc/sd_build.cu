@@ -112,6 +112,7 @@ __device__ __forceinline__ void check_index(const int* __restrict__ idx, int64_t
 // edge-mesh vertices, triangle-mesh vertices, edge indices, triangle indices)
 __global__ void k_validate(Geo g, BuildScalars* bs)
 {
+    sdsort::pdl_wait_and_release();     // (launched as k_init's dependent)
     switch (blockIdx.y) {
     case 0: check_vertices(g.P, g.np, bs); break;
     case 1: check_vertices(g.EV, g.nev, bs); break;
@@ -130,10 +131,12 @@ struct InitJob {
     int* ecnt; int nev;
     int* vcnt; int ntv;
     int* hcnt; unsigned long long* hkeys; int hcap;
+    uint32_t* hist; int nhist;          // the primitive sort's scratch words
 };
 
 __global__ void k_init(InitJob J)
 {
+    sdsort::pdl_release();      // k_validate may launch
     const int t0 = blockIdx.x * blockDim.x + threadIdx.x, st = gridDim.x * blockDim.x;
     if (t0 == 0) {
         BuildScalars b;
@@ -146,6 +149,7 @@ __global__ void k_init(InitJob J)
     }
     for (int i = t0; i < J.nparams; i += st) J.params[i] = 0.f;
     for (int i = t0; i < J.nnodes4; i += st) J.nodes[i] = make_int4(0, 0, 0, 0);
+    for (int i = t0; i < J.nhist; i += st) J.hist[i] = 0u;
     for (int i = t0; i < J.nev; i += st) J.ecnt[i] = 0;
     for (int i = t0; i < J.ntv; i += st) J.vcnt[i] = 0;
     for (int i = t0; i < J.hcap; i += st) { J.hcnt[i] = 0; J.hkeys[i] = ~0ull; }
@@ -229,11 +233,11 @@ __global__ void k_edge_params(const int* __restrict__ E, int ne, int nev, const 
 }
 
 // --- Morton codes (fp32 centroid in a fixed operation order) ---------------
-__global__ void k_morton(Geo g, const BuildScalars* bs, unsigned long long* __restrict__ codes,
-                         unsigned long long* __restrict__ keys, int* __restrict__ vals)
+// the Morton code of primitive i (written to codes, keys and its index to vals)
+__device__ __forceinline__ unsigned long long morton_code(const Geo& g, const BuildScalars* bs, int i,
+                                                          unsigned long long* codes, unsigned long long* keys,
+                                                          int* vals)
 {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= g.n) return;
     float lo[3], hi[3];
     for (int j = 0; j < 3; ++j) { lo[j] = key2f(bs->box[j]); hi[j] = key2f(bs->box[3 + j]); }
     int nvx = prim_nv(g, i);
@@ -269,6 +273,27 @@ __global__ void k_morton(Geo g, const BuildScalars* bs, unsigned long long* __re
     codes[i] = code;
     keys[i] = code;
     vals[i] = i;
+    return code;
+}
+
+// (blocks of 256 threads over a grid-stride loop; each block also adds its
+// codes' radix digits of all eight passes to the sort's digit totals, once
+// per block, so that few blocks contend for the totals' words)
+__global__ void __launch_bounds__(256) k_morton(Geo g, const BuildScalars* bs, unsigned long long* __restrict__ codes,
+                                                unsigned long long* __restrict__ keys, int* __restrict__ vals,
+                                                uint32_t* __restrict__ totals)
+{
+    __shared__ uint32_t h[8][256];
+    sdsort::pdl_release();      // the sort's first pass may launch
+    for (int p = 0; p < 8; ++p) h[p][threadIdx.x] = 0;
+    __syncthreads();
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.n; i += gridDim.x * blockDim.x)
+        sdsort::count_key(h, morton_code(g, bs, i, codes, keys, vals), 8);
+    __syncthreads();
+    for (int p = 0; p < 8; ++p) {
+        const uint32_t c = h[p][threadIdx.x];
+        if (c) atomicAdd(&totals[256 * p + threadIdx.x], c);
+    }
 }
 
 // --- binary radix tree over buckets (Karras 2012) --------------------------
@@ -280,11 +305,36 @@ __device__ __forceinline__ int bucket_prefix(const unsigned long long* sk, const
     return 64 + __clz(sv[(size_t)i * L] ^ sv[(size_t)j * L]);
 }
 
-__global__ void k_karras(const unsigned long long* __restrict__ sk, const int* __restrict__ sv, int L, int nb,
-                         int* __restrict__ left, int* __restrict__ right, int* __restrict__ parent_int,
-                         int2* __restrict__ range, SdNode* __restrict__ nodes)
+// Record nb - 1 is the super-root: one child (the root, or leaf 0 when the
+// tree is a single bucket) in slot 0; slot 1 is empty and never tested.
+__device__ __forceinline__ void super_root_record(SdNode* nodes, float2* lw2, int nb)
 {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    SdNode& r = nodes[nb - 1];
+    r.d.x = nb > 1 ? 0 : -1;
+    r.d.y = SD_NO_CHILD;
+    float* f = reinterpret_cast<float*>(&r);
+    for (int j = 1; j < 12; j += 2) f[j] = 0.f;
+    f[15] = 0.f;
+    lw2[nb - 1].y = 0.f;
+}
+
+// the tree's scalars from the build's atomics (one thread): the weight
+// scales, and the validation bits folded into the tree's status word
+__device__ __forceinline__ void finalize_scalars(const BuildScalars* bs, int unit, SdScalars* sc, int* status)
+{
+    sc->A_E = unit ? 1.f : (float)bs->A_E;
+    sc->A_T = unit ? 1.f : (float)bs->A_T;
+    sc->status = bs->status;
+    if (bs->status & ST_INDEX) atomicOr(status, 1 << SD_ERR_INDEX);
+    if (bs->status & ST_NONFINITE) atomicOr(status, 1 << SD_ERR_NONFINITE);
+}
+
+__device__ __forceinline__ void karras_node(int i, const unsigned long long* __restrict__ sk,
+                                            const int* __restrict__ sv, int L, int nb, int* __restrict__ left,
+                                            int* __restrict__ right, int* __restrict__ parent_int,
+                                            int2* __restrict__ range, SdNode* __restrict__ nodes,
+                                            float2* __restrict__ lw2)
+{
     if (i >= nb - 1) return;
     int d = bucket_prefix(sk, sv, L, nb, i, i + 1) - bucket_prefix(sk, sv, L, nb, i, i - 1) > 0 ? 1 : -1;
     int dmin = bucket_prefix(sk, sv, L, nb, i, i - d);
@@ -309,6 +359,7 @@ __global__ void k_karras(const unsigned long long* __restrict__ sk, const int* _
     left[i] = lref;
     right[i] = rref;
     range[i] = make_int2(lo, hi);
+    if (i == 0) super_root_record(nodes, lw2, nb);
     if (lref >= 0) parent_int[gamma] = i;
     if (rref >= 0) parent_int[gamma + 1] = i;
     nodes[i].d.x = lref;
@@ -336,9 +387,10 @@ __device__ __forceinline__ void write_slot(SdNode* nodes, float2* lw2, int rec, 
 // Aggregates without a bottom-up climb. Every node of the radix tree covers a
 // contiguous range of buckets, so its AABB (an exact fp32 min/max, the same
 // in any order of reduction), its primitive count and whether it holds only
-// points are reductions over that range. k_leaves computes every bucket's
-// own aggregates and, in each block of 1,024 buckets, the unions over every
-// aligned run of 2^k buckets (k = 0..10); k_nodes then assembles each
+// points are reductions over that range. The bucket blocks of k_after_sort
+// compute every bucket's own aggregates and, in each block of 1,024
+// buckets, the unions over every aligned run of 2^k buckets (k = 0..10);
+// k_nodes then assembles each
 // internal node from at most 2 x 10 aligned runs plus whole runs of 1,024,
 // loaded independently of one another. A run entry is two float4:
 // (lo.x, lo.y, lo.z, 1 if points only else 0) and (hi.x, hi.y, hi.z, 0).
@@ -360,15 +412,17 @@ __device__ __forceinline__ float far_weight(const BuildScalars* bs, float S, int
     return (S == 1.f) ? A : powf(A, S);
 }
 
-__global__ void __launch_bounds__(AGG_T) k_leaves(Geo g, const int* __restrict__ sorted, int L, int nb,
-                                                  float* __restrict__ leaf_box, int* __restrict__ leaf_count,
-                                                  float4* __restrict__ runs, SdNode* nodes, float2* lw2,
-                                                  const BuildScalars* bs, float S, int unit)
+// (called by every thread of a block of AGG_T threads; blk = the block's
+// index among the bucket blocks)
+__device__ __forceinline__ void leaves_block(int blk, const Geo& g, const int* __restrict__ sorted, int L, int nb,
+                                             float* __restrict__ leaf_box, int* __restrict__ leaf_count,
+                                             float4* __restrict__ runs, SdNode* nodes, float2* lw2,
+                                             const BuildScalars* bs, float S, int unit)
 {
     __shared__ float s_lo[3][AGG_T], s_hi[3][AGG_T];
     __shared__ int s_pts[AGG_T];
     const int t = threadIdx.x;
-    const int b = blockIdx.x * AGG_T + t;
+    const int b = blk * AGG_T + t;
     float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
     int pts = 1;
     if (b < nb) {
@@ -408,7 +462,7 @@ __global__ void __launch_bounds__(AGG_T) k_leaves(Geo g, const int* __restrict__
             }
             const int f = s_pts[i0] & s_pts[i1];
             s_pts[i0] = f;
-            const int64_t r = (int64_t)blockIdx.x * (AGG_T >> k) + t;       // run index at level k
+            const int64_t r = (int64_t)blk * (AGG_T >> k) + t;             // run index at level k
             if ((r << k) < nb) {
                 const int64_t e = run_level_offset(nb, k) + r;
                 runs[2 * e] = make_float4(a[0], a[1], a[2], (float)f);
@@ -423,28 +477,74 @@ __global__ void __launch_bounds__(AGG_T) k_leaves(Geo g, const int* __restrict__
 __global__ void k_nodes(int nb, int L, int n, const int2* __restrict__ range, const int* __restrict__ left,
                         const int* __restrict__ right, const int* __restrict__ parent_int,
                         const float4* __restrict__ runs, float* __restrict__ node_box, int* __restrict__ node_count,
-                        SdNode* nodes, float2* lw2, const BuildScalars* bs, float S, int unit)
+                        SdNode* nodes, float2* lw2, const BuildScalars* bs, float S, int unit, SdScalars* sc,
+                        int* status)
 {
     __shared__ int64_t s_off[AGG_LEVELS];
+    sdsort::pdl_wait_and_release();     // (launched as k_after_sort's dependent)
+    if (blockIdx.x == 0 && threadIdx.x == 0) finalize_scalars(bs, unit, sc, status);
     if (threadIdx.x < AGG_LEVELS) s_off[threadIdx.x] = run_level_offset(nb, threadIdx.x);
     __syncthreads();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nb - 1) return;
-    const float wfar = far_weight(bs, S, unit);
-    const int2 rg = __ldg(&range[i]);
-    const int a = rg.x, e = rg.y + 1;       // buckets [a, e)
+    const bool live = i < nb - 1;
+    if (!__any_sync(0xffffffffu, live)) return;     // (a warp-uniform exit)
+    const int lane = threadIdx.x & 31;
+    int a = 0, e = 0;       // buckets [a, e)
+    if (live) {
+        const int2 rg = __ldg(&range[i]);
+        a = rg.x;
+        e = rg.y + 1;
+    }
     float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
     float pts = 1.f;
+    // The whole runs of 1,024 buckets in [a, e), [g0, g1): for a node with
+    // more than eight of them the warp loads them together, one node at a
+    // time, and reduces them with shuffles.
+    constexpr int TOP = AGG_LEVELS - 1;
+    const int m0 = (a + (1 << TOP) - 1) >> TOP, m1 = e >> TOP;
+    const bool wide = live && m1 - m0 > 8;
+    for (unsigned wm = __ballot_sync(0xffffffffu, wide); wm; wm &= wm - 1) {
+        const int src = __ffs(wm) - 1;
+        const int r0 = __shfl_sync(0xffffffffu, m0, src), r1 = __shfl_sync(0xffffffffu, m1, src);
+        float l0 = INFINITY, l1 = INFINITY, l2 = INFINITY, h0 = -INFINITY, h1 = -INFINITY, h2 = -INFINITY, f = 1.f;
+        for (int r = r0 + lane; r < r1; r += 32) {
+            const float4 A = __ldg(&runs[2 * (s_off[TOP] + r)]), B = __ldg(&runs[2 * (s_off[TOP] + r) + 1]);
+            l0 = fminf(l0, A.x); l1 = fminf(l1, A.y); l2 = fminf(l2, A.z);
+            h0 = fmaxf(h0, B.x); h1 = fmaxf(h1, B.y); h2 = fmaxf(h2, B.z);
+            f = fminf(f, A.w);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            l0 = fminf(l0, __shfl_xor_sync(0xffffffffu, l0, o));
+            l1 = fminf(l1, __shfl_xor_sync(0xffffffffu, l1, o));
+            l2 = fminf(l2, __shfl_xor_sync(0xffffffffu, l2, o));
+            h0 = fmaxf(h0, __shfl_xor_sync(0xffffffffu, h0, o));
+            h1 = fmaxf(h1, __shfl_xor_sync(0xffffffffu, h1, o));
+            h2 = fmaxf(h2, __shfl_xor_sync(0xffffffffu, h2, o));
+            f = fminf(f, __shfl_xor_sync(0xffffffffu, f, o));
+        }
+        if (lane == src) {
+            lo[0] = l0; lo[1] = l1; lo[2] = l2;
+            hi[0] = h0; hi[1] = h1; hi[2] = h2;
+            pts = f;
+        }
+    }
+    if (!live) return;
+    const float wfar = far_weight(bs, S, unit);
+    const int g0 = wide ? m0 << TOP : e, g1 = wide ? m1 << TOP : e;
     int x = a;
     while (x < e) {
-        // the next eight aligned runs in [x, e), largest first at each step
+        // the next eight aligned runs in [x, e) outside [g0, g1), largest
+        // first at each step
         int64_t ent[8];
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
             ent[q] = -1;
+            if (x == g0) x = g1;
             if (x < e) {
+                const int lim = x < g0 ? g0 : e;
                 int k = x ? __ffs(x) - 1 : AGG_LEVELS - 1;
-                k = min(min(k, AGG_LEVELS - 1), 31 - __clz(e - x));
+                k = min(min(k, AGG_LEVELS - 1), 31 - __clz(lim - x));
                 ent[q] = s_off[k] + (x >> k);
                 x += 1 << k;
             }
@@ -466,6 +566,7 @@ __global__ void k_nodes(int nb, int L, int n, const int2* __restrict__ range, co
             hi[0] = fmaxf(hi[0], B[q].x); hi[1] = fmaxf(hi[1], B[q].y); hi[2] = fmaxf(hi[2], B[q].z);
             pts = fminf(pts, A[q].w);
         }
+        if (x == g0) x = g1;
     }
     const int count = min((int64_t)e * L, (int64_t)n) - a * L;
     for (int j = 0; j < 3; ++j) { node_box[6 * i + j] = lo[j]; node_box[6 * i + 3 + j] = hi[j]; }
@@ -488,24 +589,18 @@ __global__ void k_nodes(int nb, int L, int n, const int2* __restrict__ range, co
     }
 }
 
+// the super-root's own fields when the tree is a single bucket (with two
+// or more buckets the topology kernel writes them)
 __global__ void k_super_root(SdNode* nodes, float2* lw2, int nb)
 {
-    SdNode& r = nodes[nb - 1];
-    r.d.x = nb > 1 ? 0 : -1;
-    r.d.y = SD_NO_CHILD;
-    float* f = reinterpret_cast<float*>(&r);
-    for (int j = 1; j < 12; j += 2) f[j] = 0.f;   // slot 1 is empty
-    f[15] = 0.f;
-    lw2[nb - 1].y = 0.f;   // (the empty slot is never tested)
+    super_root_record(nodes, lw2, nb);
 }
 
-// the tree's scalars from the build's atomics (one thread): weight scales,
-// scene box for query codes, and the validation bits folded into the
-// tree's status word
 // the scene box into the tree's scalars, as soon as validation has reduced
 // it (the query order needs nothing else of the tree)
 __global__ void k_box(const BuildScalars* bs, int n, SdScalars* sc)
 {
+    sdsort::pdl_wait_and_release();     // (launched as k_validate's dependent)
     if (threadIdx.x || blockIdx.x) return;
     for (int j = 0; j < 3; ++j) {
         float lo = n ? key2f(bs->box[j]) : 0.f, hi = n ? key2f(bs->box[3 + j]) : 0.f;
@@ -516,21 +611,19 @@ __global__ void k_box(const BuildScalars* bs, int n, SdScalars* sc)
     }
 }
 
+// the tree's scalars when there are no internal nodes (k_nodes does this
+// otherwise)
 __global__ void k_finalize(const BuildScalars* bs, int unit, SdScalars* sc, int* status)
 {
     if (threadIdx.x || blockIdx.x) return;
-    sc->A_E = unit ? 1.f : (float)bs->A_E;
-    sc->A_T = unit ? 1.f : (float)bs->A_T;
-    sc->status = bs->status;
-    if (bs->status & ST_INDEX) atomicOr(status, 1 << SD_ERR_INDEX);
-    if (bs->status & ST_NONFINITE) atomicOr(status, 1 << SD_ERR_NONFINITE);
+    finalize_scalars(bs, unit, sc, status);
 }
 
 // primitives in leaf order
-__global__ void k_gather(Geo g, const int* __restrict__ sorted, const float* __restrict__ params,
-                         float4* __restrict__ hdr, float4* __restrict__ ext, int* __restrict__ sorted_out)
+__device__ __forceinline__ void gather_prim(int k, const Geo& g, const int* __restrict__ sorted,
+                                            const float* __restrict__ params, float4* __restrict__ hdr,
+                                            float4* __restrict__ ext, int* __restrict__ sorted_out)
 {
-    int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= g.n) return;
     int p = sorted[k];
     sorted_out[k] = p;
@@ -550,6 +643,40 @@ __global__ void k_gather(Geo g, const int* __restrict__ sorted, const float* __r
     hdr[k] = make_float4(a.x, a.y, a.z, (float)SD_KIND_TRI);
     ext[2 * k] = make_float4(b.x - a.x, b.y - a.y, b.z - a.z, params[2 * p]);
     ext[2 * k + 1] = make_float4(c.x - a.x, c.y - a.y, c.z - a.z, params[2 * p + 1]);
+}
+
+// After the sort, in one launch: the radix tree's topology (Karras), every
+// bucket's aggregates and aligned runs, and the primitives in leaf order.
+// Blocks [0, nbk) take the topology, the next nbl blocks the buckets, the
+// rest the gather (a block-uniform split; only the bucket blocks use
+// barriers).
+struct AfterSort {
+    Geo g;
+    const unsigned long long* sk; const int* sv; int L; int nb;
+    int* left; int* right; int* parent_int; int2* range;
+    SdNode* nodes; float2* lw2;
+    float* leaf_box; int* leaf_count; float4* runs;
+    const BuildScalars* bs; float S; int unit;
+    const float* params; float4* hdr; float4* ext; int* sorted_out;
+    int nbk, nbl;
+};
+
+__global__ void __launch_bounds__(AGG_T) k_after_sort(AfterSort A)
+{
+    sdsort::pdl_release();      // the node kernel may launch
+    int blk = blockIdx.x;
+    if (blk < A.nbk) {
+        const int i = blk * AGG_T + threadIdx.x;
+        karras_node(i, A.sk, A.sv, A.L, A.nb, A.left, A.right, A.parent_int, A.range, A.nodes, A.lw2);
+        return;
+    }
+    blk -= A.nbk;
+    if (blk < A.nbl) {
+        leaves_block(blk, A.g, A.sv, A.L, A.nb, A.leaf_box, A.leaf_count, A.runs, A.nodes, A.lw2, A.bs, A.S, A.unit);
+        return;
+    }
+    blk -= A.nbl;
+    gather_prim(blk * AGG_T + threadIdx.x, A.g, A.sv, A.params, A.hdr, A.ext, A.sorted_out);
 }
 
 inline int nblk(int64_t n, int t) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + t - 1) / t, 1 << 20)); }
@@ -682,6 +809,28 @@ static void fill_info(sd_tree* t, const SdScalars& hs)
     t->info_ready = true;
 }
 
+// Launches a kernel as the programmatic dependent of the kernel before it
+// on `st` (it may start while that one finishes; the kernel itself waits
+// for its predecessor before touching memory); an ordinary launch if the
+// attribute is refused.
+template <typename... P, typename... A>
+void launch_dependent(void (*kern)(P...), dim3 grid, dim3 block, cudaStream_t st, A... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    if (cudaLaunchKernelEx(&cfg, kern, args...) != cudaSuccess) {
+        cudaGetLastError();
+        kern<<<grid, block, 0, st>>>(args...);
+    }
+}
+
 extern "C" int sd_build(const sd_geometry* g, float alpha, float beta, const sd_build_opts* opts_in,
                         void* stream, sd_tree** out)
 {
@@ -807,11 +956,13 @@ extern "C" int sd_build(const sd_geometry* g, float alpha, float beta, const sd_
         InitJob J;
         J.bs = bs; J.status = t->status;
         J.params = t->params; J.nparams = 2 * std::max(n, 1);
-        J.nodes = (int4*)t->nodes; J.nnodes4 = 4 * std::max(nb, 1);
+        // every record of a non-empty tree is written in full below
+        J.nodes = (int4*)t->nodes; J.nnodes4 = n > 0 ? 0 : 4 * std::max(nb, 1);
         J.ecnt = ecnt; J.nev = geo.ne ? geo.nev : 0;
         J.vcnt = vcnt; J.ntv = geo.nf ? geo.ntv : 0;
         J.hcnt = hcnt; J.hkeys = hkeys; J.hcap = geo.nf ? (int)hcap : 0;
-        int work = std::max({J.nparams, J.nnodes4, J.nev, J.ntv, J.hcap});
+        J.hist = hist; J.nhist = (int)sdsort::hist_words(std::max(n, 1));
+        int work = std::max({J.nparams, J.nnodes4, J.nev, J.ntv, J.hcap, J.nhist});
         ++nl;
         k_init<<<std::min(nblk(work, T), 1024), T, 0, st>>>(J);
     }
@@ -819,9 +970,9 @@ extern "C" int sd_build(const sd_geometry* g, float alpha, float beta, const sd_
     {
         int64_t most = std::max<int64_t>({geo.np, geo.nev, geo.ntv, 2 * (int64_t)geo.ne, 3 * (int64_t)geo.nf, 1});
         ++nl;
-        k_validate<<<dim3(std::min(nblk(most, T), 1024), 5), T, 0, st>>>(geo, bs);
+        launch_dependent(k_validate, dim3(std::min(nblk(most, T), 1024), 5), dim3(T), st, geo, bs);
         ++nl;
-        k_box<<<1, 32, 0, st>>>(bs, n, t->sc);
+        launch_dependent(k_box, dim3(1), dim3(32), st, (const BuildScalars*)bs, n, t->sc);
         // with deferred checks the build returns at once: mark the point
         // after which the scene box is final (sd_query_order waits for it,
         // not for the whole build)
@@ -840,18 +991,15 @@ extern "C" int sd_build(const sd_geometry* g, float alpha, float beta, const sd_
 
     // The weight parameters (incidence counts, App. C.2-C.3) do not feed the
     // Morton codes, the sort or the topology: they run on the side stream
-    // from here on, and the leaf-order gather and the bucket aggregates
-    // follow them there once the sort is done, beside the topology; the
-    // internal nodes' aggregates (which need A and the topology) and the end
-    // of the build wait for them. Without a side stream everything stays on
-    // `st`.
+    // from here on, beside the Morton codes and the sort, and the build
+    // stream waits for them after the sort (the leaf-order gather and the
+    // aggregates need them). Without a side stream everything stays on `st`.
     cudaStream_t ps = st;
-    cudaEvent_t ev_fork = nullptr, ev_sorted = nullptr, ev_gather = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_params = nullptr;
     if (n > 0 && (geo.ne || geo.nf)) {
         cudaStream_t sd = side_stream(dev);
         if (sd && cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming) == cudaSuccess &&
-            cudaEventCreateWithFlags(&ev_sorted, cudaEventDisableTiming) == cudaSuccess &&
-            cudaEventCreateWithFlags(&ev_gather, cudaEventDisableTiming) == cudaSuccess &&
+            cudaEventCreateWithFlags(&ev_params, cudaEventDisableTiming) == cudaSuccess &&
             cudaEventRecord(ev_fork, st) == cudaSuccess && cudaStreamWaitEvent(sd, ev_fork, 0) == cudaSuccess) {
             ps = sd;
         }
@@ -874,44 +1022,52 @@ extern "C" int sd_build(const sd_geometry* g, float alpha, float beta, const sd_
         k_tri_params<<<nblk(geo.nf, T), T, 0, ps>>>(geo.F, geo.nf, geo.ntv, vcnt, hkeys, hcnt, hcap - 1, t->params,
                                                      geo.np + geo.ne, bs);
     }
+    if (ps != st) cudaEventRecord(ev_params, ps);
     if (n > 0) {
         // Morton order
         ++nl;
-        k_morton<<<nblk(n, T), T, 0, st>>>(geo, bs, (unsigned long long*)t->codes, k0, v0);
-        int where = sdsort::sort_pairs<unsigned long long, int>(k0, v0, k1, v1, n, 64, hist, st, &nl);
+        int nsm = 0;
+        if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1) {
+            cudaGetLastError();
+            nsm = 1;
+        }
+        k_morton<<<std::min(nblk(n, T), 2 * nsm), T, 0, st>>>(geo, bs, (unsigned long long*)t->codes, k0, v0,
+                                                              sdsort::digit_totals(hist, n, 8));
+        int where = sdsort::sort_pairs<unsigned long long, int>(k0, v0, k1, v1, n, 64, hist, st, &nl, true);
         unsigned long long* sk = where ? k1 : k0;
         int* sv = where ? v1 : v0;
-        // the gather needs the sorted order and the parameters
-        if (ps != st) {
-            cudaEventRecord(ev_sorted, st);
-            cudaStreamWaitEvent(ps, ev_sorted, 0);
-        }
+        // topology, buckets and gather need the sorted order and (the last
+        // two) the weight parameters
+        if (ps != st) cudaStreamWaitEvent(st, ev_params, 0);
+        AfterSort A;
+        A.g = geo; A.sk = sk; A.sv = sv; A.L = L; A.nb = nb;
+        A.left = t->left; A.right = t->right; A.parent_int = pint; A.range = range;
+        A.nodes = t->nodes; A.lw2 = t->lw2;
+        A.leaf_box = t->leaf_box; A.leaf_count = t->leaf_count; A.runs = runs;
+        A.bs = bs; A.S = S; A.unit = t->weights_unit;
+        A.params = t->params; A.hdr = t->hdr; A.ext = t->ext; A.sorted_out = t->sorted;
+        A.nbk = nb > 1 ? nblk(nb - 1, AGG_T) : 0;
+        A.nbl = nblk(nb, AGG_T);
         ++nl;
-        k_gather<<<nblk(n, T), T, 0, ps>>>(geo, sv, t->params, t->hdr, t->ext, t->sorted);
-        // every bucket's aggregates and their aligned runs, beside the topology
-        ++nl;
-        k_leaves<<<nblk(nb, AGG_T), AGG_T, 0, ps>>>(geo, sv, L, nb, t->leaf_box, t->leaf_count, runs, t->nodes, t->lw2,
-                                                     bs, S, t->weights_unit);
-        if (ps != st) cudaEventRecord(ev_gather, ps);
-        // topology
-        if (nb > 1) {
-            ++nl;
-            k_karras<<<nblk(nb - 1, T), T, 0, st>>>(sk, sv, L, nb, t->left, t->right, pint, range, t->nodes);
-        }
-        ++nl;
-        k_super_root<<<1, 1, 0, st>>>(t->nodes, t->lw2, nb);
+        k_after_sort<<<A.nbk + A.nbl + nblk(n, AGG_T), AGG_T, 0, st>>>(A);
         // internal nodes from the runs (far-field weights use A)
-        if (ps != st) cudaStreamWaitEvent(st, ev_gather, 0);
         if (nb > 1) {
             ++nl;
-            k_nodes<<<nblk(nb - 1, T), T, 0, st>>>(nb, L, n, range, t->left, t->right, pint, runs, t->node_box,
-                                                   t->node_count, t->nodes, t->lw2, bs, S, t->weights_unit);
+            launch_dependent(k_nodes, dim3(nblk(nb - 1, T)), dim3(T), st, nb, L, n, (const int2*)range,
+                             (const int*)t->left, (const int*)t->right, (const int*)pint, (const float4*)runs,
+                             t->node_box, t->node_count, t->nodes, t->lw2, (const BuildScalars*)bs, S,
+                             t->weights_unit, t->sc, t->status);
+        } else {
+            ++nl;
+            k_super_root<<<1, 1, 0, st>>>(t->nodes, t->lw2, nb);
         }
     }
-    for (cudaEvent_t e : {ev_fork, ev_sorted, ev_gather})
+    for (cudaEvent_t e : {ev_fork, ev_params})
         if (e) cudaEventDestroy(e);
-    ++nl;
-    k_finalize<<<1, 32, 0, st>>>(bs, t->weights_unit, t->sc, t->status);
+    if (nb < 2) {
+        ++nl;
+        k_finalize<<<1, 32, 0, st>>>(bs, t->weights_unit, t->sc, t->status);
+    }
     cudaFreeAsync(tmp, st);
     sd_count_launches(nl);
 

@@ -449,10 +449,14 @@ __device__ __forceinline__ float q_unkey(unsigned k)
     return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
 }
 
-__global__ void __launch_bounds__(256) k_query_bounds(const float* __restrict__ qs, int M, unsigned* __restrict__ qb)
+// (also zeroes the order sort's nz scratch words, which the codes kernel
+// then fills with the keys' digit totals)
+__global__ void __launch_bounds__(256) k_query_bounds(const float* __restrict__ qs, int M, unsigned* __restrict__ qb,
+                                                      uint32_t* __restrict__ zero, int nz)
 {
     __shared__ unsigned sh[6];
     if (threadIdx.x < 6) sh[threadIdx.x] = 0u;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nz; i += gridDim.x * blockDim.x) zero[i] = 0u;
     __syncthreads();
     unsigned hi[3] = {0u, 0u, 0u}, nlo[3] = {0u, 0u, 0u};
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < M; t += gridDim.x * blockDim.x)
@@ -489,11 +493,9 @@ __global__ void __launch_bounds__(256) k_query_bounds(const float* __restrict__ 
 // transposition (AIP Conf. Proc. 707, 2004): undo the excess work of the
 // axes from the top bit down, Gray-encode, then interleave. The order
 // changes speed and summation order only.
-__global__ void k_query_codes(const float* __restrict__ qs, int M, const SdScalars* __restrict__ sc,
-                              const unsigned* __restrict__ qb, unsigned* __restrict__ keys, int* __restrict__ vals)
+__device__ __forceinline__ unsigned hilbert_key(const float* __restrict__ qs, int t, const SdScalars* __restrict__ sc,
+                                                const unsigned* __restrict__ qb)
 {
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= M) return;
     float c[3] = {qs[3 * t], qs[3 * t + 1], qs[3 * t + 2]};
     float l[3], ie[3];
     for (int j = 0; j < 3; ++j) {
@@ -530,8 +532,32 @@ __global__ void k_query_codes(const float* __restrict__ qs, int M, const SdScala
     unsigned code = 0;
     for (int b = 7; b >= 0; --b)
         code = (code << 3) | (((k[0] >> b) & 1u) << 2) | (((k[1] >> b) & 1u) << 1) | ((k[2] >> b) & 1u);
-    keys[t] = code;
-    vals[t] = t;
+    return code;
+}
+
+// (blocks of 256 threads over a grid-stride loop; each block also adds its
+// keys' radix digits of the three passes to the sort's digit totals, once
+// per block, so that few blocks contend for the totals' words)
+__global__ void __launch_bounds__(256) k_query_codes(const float* __restrict__ qs, int M,
+                                                     const SdScalars* __restrict__ sc, const unsigned* __restrict__ qb,
+                                                     unsigned* __restrict__ keys, int* __restrict__ vals,
+                                                     uint32_t* __restrict__ totals)
+{
+    __shared__ uint32_t h[3][256];
+    sdsort::pdl_release();      // the sort's first pass may launch
+    for (int p = 0; p < 3; ++p) h[p][threadIdx.x] = 0;
+    __syncthreads();
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < M; t += gridDim.x * blockDim.x) {
+        const unsigned code = hilbert_key(qs, t, sc, qb);
+        keys[t] = code;
+        vals[t] = t;
+        sdsort::count_key(h, code, 3);
+    }
+    __syncthreads();
+    for (int p = 0; p < 3; ++p) {
+        const uint32_t c = h[p][threadIdx.x];
+        if (c) atomicAdd(&totals[256 * p + threadIdx.x], c);
+    }
 }
 
 int sm_count()
@@ -630,14 +656,18 @@ int check_query_args(const sd_tree* t, const float* q, int64_t M, const float* v
 
 namespace {
 
-// the Hilbert keys of m queries (keys) and their indices (vals); qb is six
-// words of scratch for the queries' bounds
+// the Hilbert keys of m queries (keys) and their indices (vals), counted
+// into the sort scratch `hist` (hist_words(m, 3) words, zeroed here) for a
+// three-pass sort_pairs(..., counted = true); qb is six words of scratch
+// for the queries' bounds
 void enqueue_codes(const sd_tree* t, const float* q, int m, unsigned* qb, unsigned* keys, int* vals,
-                   cudaStream_t st, int* nl)
+                   uint32_t* hist, cudaStream_t st, int* nl)
 {
     cudaMemsetAsync(qb, 0, 6 * sizeof(unsigned), st);
-    k_query_bounds<<<std::min((m + 255) / 256, 2 * sm_count()), 256, 0, st>>>(q, m, qb);
-    k_query_codes<<<(m + 255) / 256, 256, 0, st>>>(q, m, t->sc, qb, keys, vals);
+    k_query_bounds<<<std::min((m + 255) / 256, 2 * sm_count()), 256, 0, st>>>(q, m, qb, hist,
+                                                                            (int)sdsort::hist_words(m, 3));
+    k_query_codes<<<std::min((m + 255) / 256, 2 * sm_count()), 256, 0, st>>>(q, m, t->sc, qb, keys, vals,
+                                                                             sdsort::digit_totals(hist, m, 3));
     *nl += 2;
 }
 
@@ -657,8 +687,8 @@ int compute_order(const sd_tree* t, const float* q, int m, int32_t* order, cudaS
     int nl = 0;
     // the sort's odd pass count leaves its result in the second buffer: give
     // it `order` there and start from the scratch copy
-    enqueue_codes(t, q, m, qb, k0, v1, st, &nl);
-    int where = sdsort::sort_pairs<unsigned, int>(k0, v1, k1, order, m, 24, hist, st, &nl);
+    enqueue_codes(t, q, m, qb, k0, v1, hist, st, &nl);
+    int where = sdsort::sort_pairs<unsigned, int>(k0, v1, k1, order, m, 24, hist, st, &nl, true);
     if (!where) cudaMemcpyAsync(order, v1, sizeof(int) * (size_t)m, cudaMemcpyDeviceToDevice, st);
     sd_count_launches(nl);
     e = cudaGetLastError();
@@ -924,8 +954,8 @@ extern "C" int sd_query_noalloc(const sd_tree* t, const float* q, int64_t M, flo
     const int* order = nullptr;
     int nl = 0;
     if (m > 1) {
-        enqueue_codes(t, q, m, qb, k0, ord0, st, &nl);
-        int where = sdsort::sort_pairs<unsigned, int>(k0, ord0, k1, ord1, m, 24, hist, st, &nl);
+        enqueue_codes(t, q, m, qb, k0, ord0, hist, st, &nl);
+        int where = sdsort::sort_pairs<unsigned, int>(k0, ord0, k1, ord1, m, 24, hist, st, &nl, true);
         order = where ? ord1 : ord0;
     }
     dispatch<false>(t, q, m, order, value, grad, nullptr, 0, work, st);
@@ -956,8 +986,8 @@ int order_into(const sd_tree* t, const float* q, int m, int32_t* order, void* sc
     int nl = 0;
     // the sort's odd pass count leaves its result in the second buffer: give
     // it `order` there and start from the scratch copy
-    enqueue_codes(t, q, m, qb, k0, v1, st, &nl);
-    int where = sdsort::sort_pairs<unsigned, int>(k0, v1, k1, order, m, 24, hist, st, &nl);
+    enqueue_codes(t, q, m, qb, k0, v1, hist, st, &nl);
+    int where = sdsort::sort_pairs<unsigned, int>(k0, v1, k1, order, m, 24, hist, st, &nl, true);
     if (!where) cudaMemcpyAsync(order, v1, sizeof(int) * (size_t)m, cudaMemcpyDeviceToDevice, st);
     sd_count_launches(nl);
     return sd_cuda_status(cudaGetLastError());
