@@ -577,14 +577,21 @@ def _extras(args, c, V, F, q, dev, M):
     tb = e0.elapsed_time(e1)
     res["plain"] = {"value": M / (tb / 1e3), "unit": UNIT, "ms": tb, "what": "sd_query_brute, all pairs"}
     del sd
-    # end to end: pinned host inputs -> device, build + order + query, result -> pinned host
-    hV = torch.from_numpy(c["V"]).pin_memory()
-    hF = torch.from_numpy(c["F"]).pin_memory()
+    # end to end: pinned host inputs -> device, build + order + query, result -> pinned host.
+    # The mesh (vertices and faces) travels as one copy and the result (values
+    # and gradients) as one: both sides hold them in one buffer each.
+    nvb, nfb = V.numel() * 4, F.numel() * 4
+    hmesh = torch.empty(nvb + nfb, dtype=torch.uint8).pin_memory()
+    hmesh[:nvb].view(torch.float32).copy_(torch.from_numpy(c["V"]).reshape(-1))
+    hmesh[nvb:].view(torch.int32).copy_(torch.from_numpy(c["F"]).reshape(-1))
+    dmesh = torch.empty(nvb + nfb, dtype=torch.uint8, device=dev)
+    dV = dmesh[:nvb].view(torch.float32).view(V.shape)
+    dF = dmesh[nvb:].view(torch.int32).view(F.shape)
     hq = torch.from_numpy(c["queries"]).pin_memory()
-    hv = torch.empty(M).pin_memory()
-    hg = torch.empty(M, 3).pin_memory()
-    dV, dF, dq = torch.empty_like(V), torch.empty_like(F), torch.empty_like(q)
-    dv, dg = torch.empty(M, device=dev), torch.empty(M, 3, device=dev)
+    dq = torch.empty_like(q)
+    hout = torch.empty(4 * M).pin_memory()
+    dout = torch.empty(4 * M, device=dev)
+    dv, dg = dout[:M], dout[M:].view(M, 3)
 
     side = torch.cuda.Stream(device=dev)
     fork, join = torch.cuda.Event(), torch.cuda.Event()
@@ -594,8 +601,7 @@ def _extras(args, c, V, F, q, dev, M):
         # mesh upload and build on the main stream; query upload and order on
         # a second one (from the build's scene box on); then the query
         fork.record(stream)
-        dV.copy_(hV, non_blocking=True)
-        dF.copy_(hF, non_blocking=True)
+        dmesh.copy_(hmesh, non_blocking=True)
         s = SmoothDistance(tris=(dV, dF), alpha=args.alpha, beta=args.beta, leaf_size=args.leaf_size, device=dev,
                            check=False)
         side.wait_event(fork)
@@ -605,8 +611,7 @@ def _extras(args, c, V, F, q, dev, M):
         join.record(side)
         stream.wait_event(join)
         s.query(dq, out=(dv, dg), order=de)
-        hv.copy_(dv, non_blocking=True)
-        hg.copy_(dg, non_blocking=True)
+        hout.copy_(dout, non_blocking=True)
 
     for _ in range(2):
         e2e_step()
@@ -619,8 +624,8 @@ def _extras(args, c, V, F, q, dev, M):
     torch.cuda.synchronize()
     te = e0.elapsed_time(e1) / n
     res["e2e"] = {"value": M / (te / 1e3), "unit": UNIT, "ms_per_step": te,
-                  "h2d_bytes_per_step": int(hV.numel() * 4 + hF.numel() * 4 + hq.numel() * 4),
-                  "d2h_bytes_per_step": int(hv.numel() * 4 + hg.numel() * 4)}
+                  "h2d_bytes_per_step": int(hmesh.numel() + hq.numel() * 4),
+                  "d2h_bytes_per_step": int(hout.numel() * 4)}
     res["cpu_baseline"] = _cpu_baseline(c, args, min_seconds=10.0)
     res["pose"] = _pose_leg(args, dev)
     res["batch"] = _batch_leg(args, dev)

@@ -1,11 +1,14 @@
 // Stable LSD radix sort (8-bit digits) of key/value pairs in device memory,
-// one launch per digit pass ("onesweep"): a first kernel counts every
-// digit of every pass at once; each pass kernel then takes tiles in
-// launch order from an atomic counter, publishes its tile's digit counts,
-// finds the counts of all earlier tiles by a decoupled look-back over their
-// published (count, flag) words, and scatters its keys stably (equal digits
-// ranked inside the tile with warp match masks). Used for the Morton order
-// of primitives (64-bit keys) and of queries (32-bit keys).
+// one launch per digit pass ("onesweep"): the digits of every pass are
+// counted at once first (by a counting kernel, or by the kernel that makes
+// the keys); each pass kernel then takes tiles in launch order from an
+// atomic counter, loads its keys and values, ranks them inside the tile
+// (equal digits in order, by warp match masks), publishes the tile's digit
+// counts, finds the counts of all earlier tiles by a decoupled look-back
+// over their published (count, flag) words, up to eight tiles a round, and
+// scatters its keys stably. Each pass is launched as the programmatic
+// dependent of the kernel before it. Used for the Morton order of
+// primitives (64-bit keys) and of queries (32-bit keys).
 //
 // The look-back only waits on tiles with smaller indices, which were taken
 // by blocks that already run; every wait is bounded all the same. A tile
