@@ -67,6 +67,13 @@ def test_build_bit_exact(name, L):
     assert info["A_E"] == sc.A_E and info["A_T"] == sc.A_T
 
 
+@pytest.mark.parametrize("name", ["tris", "ico6", "points_cap1"])
+def test_build_bit_exact_largest_leaf(name):
+    """L = 1024, the largest leaf size: 5, 80 and 129 buckets (a single
+    block of bucket runs, a wide root)."""
+    test_build_bit_exact(name, 1024)
+
+
 def test_build_errors_are_reported():
     from paper_2108_10480_gb300 import SdError
     P = synth.points_on_sphere(100, 0.0, 0)

@@ -79,6 +79,22 @@ def test_triangles_bh(ico4, alpha, beta, L):
     assert_parity(_np(v), _np(g), bv, bg, alpha, None, f"bh a={alpha} b={beta} L={L}")
 
 
+def test_largest_leaf_size(ico4):
+    """L = 1024, the largest leaf the build accepts: five buckets over the
+    5,120 triangles, so every opened leaf queues up to 1,024 primitives per
+    lane. Work counts bit-exact, values and gradients within the parity
+    bound."""
+    V, F, sc, q = ico4
+    sd = _gpu(tris=(V, F), alpha=200.0, beta=0.5, leaf_size=1024)
+    assert sd.info()["n_buckets"] == 5
+    sc.build_tree(1024)
+    bv, bg, bc, _ = sc.bh(q, 200.0, 0.5)
+    sc.build_tree(1)
+    v, g, cnt = sd.query(_t(q), counts=True)
+    assert np.array_equal(cnt.cpu().numpy(), bc)
+    assert_parity(_np(v), _np(g), bv, bg, 200.0, None, "bh L=1024")
+
+
 @pytest.fixture(scope="module")
 def ico6():
     c = synth.config2()
