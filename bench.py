@@ -594,17 +594,18 @@ def _extras(args, c, V, F, q, dev, M):
     dv, dg = dout[:M], dout[M:].view(M, 3)
 
     side = torch.cuda.Stream(device=dev)
-    fork, join = torch.cuda.Event(), torch.cuda.Event()
+    meshed, join = torch.cuda.Event(), torch.cuda.Event()
     de = torch.empty(M, dtype=torch.int32, device=dev)
 
     def e2e_step():
-        # mesh upload and build on the main stream; query upload and order on
-        # a second one (from the build's scene box on); then the query
-        fork.record(stream)
+        # mesh upload and build on the main stream; query upload (once the
+        # mesh is across, so that the build's input never shares the copy
+        # bandwidth) and order on a second one; then the query
         dmesh.copy_(hmesh, non_blocking=True)
+        meshed.record(stream)
         s = SmoothDistance(tris=(dV, dF), alpha=args.alpha, beta=args.beta, leaf_size=args.leaf_size, device=dev,
                            check=False)
-        side.wait_event(fork)
+        side.wait_event(meshed)
         with torch.cuda.stream(side):
             dq.copy_(hq, non_blocking=True)
         s.query_order(dq, stream=side, out=de)
